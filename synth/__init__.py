@@ -1,0 +1,321 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and by the oracle.
+
+This module holds no arithmetic of the eigensolver: it only draws graphs (as
+undirected edge lists of int32 node pairs) and random starting blocks.  Every
+draw goes through numpy's Philox bit generator with an explicit seed, so the
+same call returns the same bytes on x86 and Arm hosts.
+
+Graph families (stand-ins for the workloads the paper evaluates on, Sec. 4):
+
+* ``sbm_edges``       stochastic block model (HPEC Graph Challenge style
+                      partitions, Sec. 4.1) with equal planted clusters;
+* ``batch_sbm``       many SBM graphs of log-uniform size;
+* ``knn_gmm_edges``   symmetrised k-nearest-neighbour graph of a Gaussian
+                      mixture;
+* ``rmat_edges``      R-MAT power-law graph (Graph500 style, Table 2);
+* closed-form graphs (cycle, path, hypercube, complete, complete bipartite,
+  star, disjoint unions) whose Laplacian spectra are known exactly.
+
+Edge lists may contain duplicates, both orientations and self loops; the
+Laplacian builders on either side are specified to symmetrise, deduplicate and
+drop self loops.  ``reattach_isolated`` implements the "isolated nodes are
+reattached by one random edge" rule of the SBM workloads.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "rng",
+    "gaussian_block",
+    "sbm_edges",
+    "reattach_isolated",
+    "batch_sbm",
+    "knn_gmm_edges",
+    "rmat_edges",
+    "cycle_edges",
+    "path_edges",
+    "hypercube_edges",
+    "complete_edges",
+    "complete_bipartite_edges",
+    "star_edges",
+    "disjoint_union",
+    "Graph",
+    "workload",
+]
+
+
+def rng(seed: int) -> np.random.Generator:
+    """Philox-backed generator; the only source of randomness in this module."""
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+def gaussian_block(n: int, cols: int, seed: int = 0) -> np.ndarray:
+    """Row-major n x cols float64 block of standard normal numbers (the V0 block)."""
+    return rng(seed).standard_normal((n, cols))
+
+
+@dataclass
+class Graph:
+    """An undirected graph on nodes 0..n-1 given as an edge list."""
+
+    n: int
+    src: np.ndarray  # int32
+    dst: np.ndarray  # int32
+    name: str = ""
+    labels: np.ndarray | None = None  # planted cluster of each node, if any
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.src.shape[0])
+
+
+def _as_graph(n, src, dst, name, labels=None) -> Graph:
+    return Graph(int(n), np.ascontiguousarray(src, dtype=np.int32),
+                 np.ascontiguousarray(dst, dtype=np.int32), name, labels)
+
+
+# ----------------------------------------------------------------------------
+# closed-form families
+# ----------------------------------------------------------------------------
+
+def cycle_edges(n: int) -> Graph:
+    i = np.arange(n, dtype=np.int64)
+    return _as_graph(n, i, (i + 1) % n, f"cycle{n}")
+
+
+def path_edges(n: int) -> Graph:
+    i = np.arange(n - 1, dtype=np.int64)
+    return _as_graph(n, i, i + 1, f"path{n}")
+
+
+def hypercube_edges(d: int) -> Graph:
+    n = 1 << d
+    i = np.arange(n, dtype=np.int64)
+    src = np.concatenate([i for _ in range(d)])
+    dst = np.concatenate([i ^ (1 << t) for t in range(d)])
+    keep = src < dst
+    return _as_graph(n, src[keep], dst[keep], f"hypercube{d}")
+
+
+def complete_edges(n: int) -> Graph:
+    iu = np.triu_indices(n, 1)
+    return _as_graph(n, iu[0], iu[1], f"K{n}")
+
+
+def complete_bipartite_edges(a: int, b: int) -> Graph:
+    u = np.repeat(np.arange(a), b)
+    v = np.tile(np.arange(b), a) + a
+    return _as_graph(a + b, u, v, f"K{a},{b}")
+
+
+def star_edges(leaves: int) -> Graph:
+    v = np.arange(1, leaves + 1)
+    return _as_graph(leaves + 1, np.zeros_like(v), v, f"star{leaves}")
+
+
+def disjoint_union(*graphs: Graph) -> Graph:
+    off = 0
+    src, dst = [], []
+    for g in graphs:
+        src.append(g.src.astype(np.int64) + off)
+        dst.append(g.dst.astype(np.int64) + off)
+        off += g.n
+    return _as_graph(off, np.concatenate(src), np.concatenate(dst),
+                     "+".join(g.name for g in graphs))
+
+
+# ----------------------------------------------------------------------------
+# random families
+# ----------------------------------------------------------------------------
+
+def _unique_pairs(u: np.ndarray, v: np.ndarray, n: int) -> np.ndarray:
+    lo = np.minimum(u, v).astype(np.int64)
+    hi = np.maximum(u, v).astype(np.int64)
+    return np.unique(lo * n + hi)
+
+
+def _sample_pairs(g, k, draw, n):
+    """k distinct unordered pairs drawn uniformly by rejection from ``draw``."""
+    keys = np.empty(0, dtype=np.int64)
+    while keys.shape[0] < k:
+        need = k - keys.shape[0]
+        m = int(need * 1.1) + 16
+        u, v = draw(m)
+        ok = u != v
+        new = _unique_pairs(u[ok], v[ok], n)
+        keys = np.union1d(keys, new)
+        if keys.shape[0] > k:
+            keys = g.permutation(keys)[:k]
+            keys.sort()
+    return keys
+
+
+def sbm_edges(n: int, c: int, *, p_in: float | None = None, p_out: float | None = None,
+              d_in: float | None = None, d_out: float | None = None, seed: int = 1,
+              reattach: bool = True) -> Graph:
+    """Stochastic block model on n nodes with c planted clusters.
+
+    Cluster sizes are floor(n/c) with the first n mod c clusters one larger;
+    node ids are cluster-contiguous.  Each unordered pair is an edge
+    independently with probability p_in (same cluster) or p_out (different
+    clusters); the edge count of each population is drawn Binomial and the
+    pairs uniformly without replacement, which is the same distribution.
+    Expected degrees may be given instead: p_in = d_in/(n_c - 1),
+    p_out = d_out/(n - n_c) with n_c the mean cluster size.
+    """
+    g = rng(seed)
+    sizes = np.full(c, n // c, dtype=np.int64)
+    sizes[: n % c] += 1
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    labels = np.repeat(np.arange(c, dtype=np.int32), sizes)
+    nc = n / c
+    if p_in is None:
+        p_in = d_in / (nc - 1.0)
+    if p_out is None:
+        p_out = d_out / (n - nc)
+    keys = []
+    for a in range(c):
+        s, sz = int(starts[a]), int(sizes[a])
+        m_pairs = sz * (sz - 1) // 2
+        k = int(g.binomial(m_pairs, p_in)) if m_pairs > 0 else 0
+        if k > 0:
+            draw = lambda m, s=s, sz=sz: (g.integers(s, s + sz, m), g.integers(s, s + sz, m))
+            keys.append(_sample_pairs(g, k, draw, n))
+    m_out = (n * (n - 1)) // 2 - int(np.sum(sizes * (sizes - 1) // 2))
+    k_out = int(g.binomial(m_out, p_out)) if m_out > 0 else 0
+    if k_out > 0:
+        def draw_out(m):
+            u = g.integers(0, n, m)
+            v = g.integers(0, n, m)
+            same = labels[u] == labels[v]
+            return u[~same], v[~same]
+        keys.append(_sample_pairs(g, k_out, draw_out, n))
+    keys = np.concatenate(keys) if keys else np.empty(0, dtype=np.int64)
+    src, dst = keys // n, keys % n
+    if reattach:
+        src, dst = reattach_isolated(n, src, dst, g)
+    return _as_graph(n, src, dst, f"sbm{n}c{c}", labels)
+
+
+def reattach_isolated(n: int, src: np.ndarray, dst: np.ndarray, g: np.random.Generator):
+    """Give every node with no neighbour (self loops ignored) one random edge.
+
+    The isolated set is computed once; each isolated node, in increasing id
+    order, draws its partner uniformly from the other n - 1 nodes.
+    """
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    ok = src != dst
+    deg = np.bincount(src[ok], minlength=n) + np.bincount(dst[ok], minlength=n)
+    iso = np.flatnonzero(deg == 0)
+    if iso.size == 0 or n < 2:
+        return src, dst
+    j = g.integers(0, n - 1, iso.size)
+    j = j + (j >= iso)  # uniform over [0, n) \ {i}
+    return np.concatenate([src, iso]), np.concatenate([dst, j])
+
+
+def batch_sbm(n_graphs: int = 512, n_lo: int = 2000, n_hi: int = 200000, c_lo: int = 4,
+              c_hi: int = 32, d_in: float = 12.0, d_out: float = 1.5, seed: int = 4,
+              base_seed: int = 1000):
+    """Many independent SBM graphs: sizes log-uniform in [n_lo, n_hi], c uniform."""
+    g = rng(seed)
+    ns = np.floor(np.exp(g.uniform(math.log(n_lo), math.log(n_hi), n_graphs))).astype(np.int64)
+    cs = g.integers(c_lo, c_hi + 1, n_graphs)
+    return [sbm_edges(int(ns[i]), int(cs[i]), d_in=d_in, d_out=d_out, seed=base_seed + i)
+            for i in range(n_graphs)]
+
+
+def knn_gmm_edges(n: int, dim: int = 16, n_comp: int = 50, knn: int = 10, seed: int = 3,
+                  box: float = 10.0) -> Graph:
+    """Symmetrised, unweighted k-NN graph of points from an isotropic Gaussian mixture.
+
+    Component means are uniform in [-box, box]^dim, unit variance, uniform
+    weights; points stay in draw order.  Neighbours are exact Euclidean
+    nearest neighbours (ties to the lower index), found with a KD-tree.
+    """
+    from scipy.spatial import cKDTree
+
+    g = rng(seed)
+    means = g.uniform(-box, box, (n_comp, dim))
+    comp = g.integers(0, n_comp, n)
+    x = means[comp] + g.standard_normal((n, dim))
+    tree = cKDTree(x)
+    _, idx = tree.query(x, k=knn + 1, workers=-1)
+    src = np.repeat(np.arange(n, dtype=np.int64), knn + 1)
+    dst = idx.reshape(-1).astype(np.int64)
+    keep = src != dst
+    return _as_graph(n, src[keep], dst[keep], f"knn{n}", comp.astype(np.int32))
+
+
+def rmat_edges(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
+               c: float = 0.19, seed: int = 5, chunk: int = 1 << 22) -> Graph:
+    """R-MAT sampler (Graph500 parameters by default), no vertex permutation.
+
+    edge_factor * 2^scale directed samples; each picks one quadrant per level
+    with probabilities (a, b, c, 1-a-b-c).
+    """
+    n = 1 << scale
+    m = edge_factor * n
+    g = rng(seed)
+    srcs, dsts = [], []
+    ab = a + b
+    c_norm = c / (1.0 - ab)
+    a_norm = a / ab
+    for lo in range(0, m, chunk):
+        k = min(chunk, m - lo)
+        u = np.zeros(k, dtype=np.int64)
+        v = np.zeros(k, dtype=np.int64)
+        for lvl in range(scale):
+            r1 = g.random(k)
+            r2 = g.random(k)
+            ibit = r1 > ab
+            jbit = np.where(ibit, r2 > c_norm, r2 > a_norm)
+            u |= ibit.astype(np.int64) << lvl
+            v |= jbit.astype(np.int64) << lvl
+        srcs.append(u)
+        dsts.append(v)
+    src = np.concatenate(srcs)
+    dst = np.concatenate(dsts)
+    src, dst = reattach_isolated(n, src, dst, g)
+    return _as_graph(n, src, dst, f"rmat{scale}")
+
+
+# ----------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------
+
+def workload(name: str) -> dict:
+    """Graph plus solver parameters of the named benchmark workloads.
+
+    sbm10k   : SBM N=10,000, 10 clusters, p_in=1e-3, p_out=2e-5, k=10, b=5, m=11, act_max=30
+    sbm1m    : SBM N=1,000,000, 100 clusters, d_in=16, d_out=2, k=100, b=20, m=15, act_max=300
+    knn2m    : kNN-GMM 2,000,000 x 16-D, 50 components, 10-NN, k=50, b=10, m=13, act_max=150
+    rmat24   : R-MAT scale 24, ef 16, k=64, b=16, m=15, act_max=192
+    Scaled-down variants (for tests) take a suffix, e.g. ``sbm1m@50000`` keeps
+    the per-node statistics with fewer nodes.
+    """
+    base, _, size = name.partition("@")
+    tol = 1e-8
+    if base == "sbm10k":
+        n = int(size) if size else 10000
+        gr = sbm_edges(n, 10, p_in=1e-3 * 10000 / n, p_out=2e-5 * 10000 / n, seed=1)
+        return dict(graph=gr, k=10, b=5, m=11, act_max=30, tol=tol, v0_seed=0)
+    if base == "sbm1m":
+        n = int(size) if size else 1000000
+        c = 100 if n >= 100000 else max(4, n // 10000)
+        gr = sbm_edges(n, c, d_in=16.0, d_out=2.0, seed=2)
+        return dict(graph=gr, k=c, b=20, m=15, act_max=300, tol=tol, v0_seed=0)
+    if base == "knn2m":
+        n = int(size) if size else 2000000
+        gr = knn_gmm_edges(n, seed=3)
+        return dict(graph=gr, k=50, b=10, m=13, act_max=150, tol=tol, v0_seed=0)
+    if base == "rmat24":
+        scale = int(size) if size else 24
+        gr = rmat_edges(scale, seed=5)
+        return dict(graph=gr, k=64, b=16, m=15, act_max=192, tol=tol, v0_seed=0)
+    raise KeyError(name)
