@@ -1,0 +1,197 @@
+/*
+ * bchdav.h -- C ABI of the GB300 block Chebyshev-Davidson eigensolver.
+ *
+ * Problem (Eqs. (1)-(2) of the paper): for the symmetric normalized Laplacian
+ * A = I - D^{-1/2} S D^{-1/2} of an undirected graph with N nodes, find the k
+ * smallest eigenvalues 0 <= lambda_1 <= ... <= lambda_k <= 2 and eigenvectors
+ * V (N x k) with A V = V Lambda_k.  The method is Algorithm 2 (block
+ * Chebyshev-Davidson with inner-outer restart) with the Chebyshev filter of
+ * Algorithm 3 and the analytic spectrum bounds [0, 2].
+ *
+ * Conventions shared by every entry point:
+ *  - All array arguments are DEVICE pointers unless stated otherwise.  Dense
+ *    blocks are row-major: element (i, j) of an N x w block with leading
+ *    dimension ld sits at p[i * ld + j], ld >= w.
+ *  - The caller owns every array it passes in; the library owns its workspace
+ *    (kept in the handle) and the CSR arrays returned by bchdav_build_laplacian.
+ *  - Work is ordered on the handle's CUDA stream.  Functions that must decide
+ *    on data (bchdav_solve, bchdav_orthonormalize, bchdav_build_laplacian)
+ *    synchronise that stream before returning; the others only enqueue.
+ *  - Errors are returned as bchdav_status, never thrown; bchdav_last_error()
+ *    gives a message.  Invalid sizes give BCHDAV_ERR_ARG and no work is
+ *    enqueued.  A CUDA failure gives BCHDAV_ERR_CUDA.
+ *  - Nothing here allocates memory visible to the caller except
+ *    bchdav_build_laplacian.
+ */
+#ifndef BCHDAV_H
+#define BCHDAV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BCHDAV_OK = 0,
+  BCHDAV_NOT_CONVERGED = 1,   /* itmax reached; the first info.n_converged pairs are valid */
+  BCHDAV_ERR_ARG = -1,        /* invalid size, pointer or parameter */
+  BCHDAV_ERR_CSR = -2,        /* CSR structure invalid (row pointers, column range/order) */
+  BCHDAV_ERR_OOM = -3,        /* workspace allocation failed */
+  BCHDAV_ERR_CUDA = -4,       /* a CUDA call or kernel launch failed */
+  BCHDAV_ERR_NONFINITE = -5,  /* NaN or Inf appeared in the iteration */
+  BCHDAV_ERR_TIMEOUT = -6     /* a bounded device-side wait gave up */
+} bchdav_status;
+
+typedef enum {
+  BCHDAV_PREC_FP64 = 0,   /* every step in float64 */
+  BCHDAV_PREC_MIXED = 1   /* filter SpMM and recurrence in float32, the rest float64 */
+} bchdav_precision;
+
+typedef struct bchdav_handle_s* bchdav_handle;
+
+/* The matrix A in CSR form (device arrays).  Rows ascending, column indices
+ * ascending and in [0, n) within each row, nnz = rowptr[n] < 2^31.
+ * val (float64) is required.  val_f32 is optional: when NULL and the mixed
+ * path is requested, the solver rounds val to float32 into its workspace. */
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int32_t* rowptr;   /* n + 1 */
+  const int32_t* colidx;   /* nnz */
+  const double* val;       /* nnz */
+  const float* val_f32;    /* nnz or NULL */
+} bchdav_csr;
+
+/* Optional parameters of bchdav_solve; zero-initialise for the defaults. */
+typedef struct {
+  int32_t dim_max;          /* 0: min(max(act_max + 2b, k + 30), N)  (Sec. 4 defaults) */
+  int32_t itmax;            /* 0: 1000 outer iterations */
+  int32_t precision;        /* bchdav_precision */
+  int32_t reserved0;
+  uint64_t seed;            /* seed of the random vectors the method draws (Philox4x32-10) */
+  const double* v_init;     /* optional N x k_init initial block (Algorithm 2, V_init) */
+  int32_t k_init;
+  int32_t ld_v_init;
+  int32_t record_history;   /* nonzero: keep per-iteration counters (bchdav_history) */
+  int32_t reserved1;
+} bchdav_opts;
+
+/* Results and per-component device time of one solve. */
+typedef struct {
+  int32_t iters;            /* outer iterations of Algorithm 2 */
+  int32_t n_converged;      /* locked pairs (>= k on success) */
+  int32_t n_spmm;           /* SpMM launches with A (filter + W + residual) */
+  int32_t n_replaced;       /* vectors replaced by random ones in Step 6 */
+  double max_rel_resid;     /* max_j ||A v_j - lambda_j v_j|| / ||v_j|| over the returned pairs */
+  double ms_total;
+  double ms_filter, ms_orth, ms_spmm_w, ms_h, ms_eig, ms_rot, ms_resid, ms_other;
+  double filter_bytes;      /* algorithmic bytes moved by all filter SpMM steps */
+  double filter_ms_kernels; /* device time of those steps alone (CUDA events) */
+  int64_t n_kernel_launches;/* kernels this library launched during the solve */
+} bchdav_info;
+
+/* One record per outer iteration when opts.record_history is set. */
+typedef struct {
+  int32_t it, k_c, e_c, k_act, k_sub, k_old, n_rep;
+  int32_t k_orth;           /* basis width Step 6 orthogonalised against (k_sub before Step 7) */
+  double low_nwb;
+  double max_resid;         /* max relative residual of the k_b tested pairs */
+} bchdav_iter_record;
+
+/* ---- handle ------------------------------------------------------------- */
+
+/* Create a handle bound to the current CUDA device and the given stream
+ * (cudaStream_t, NULL = legacy default stream). */
+bchdav_status bchdav_create(bchdav_handle* h, void* cuda_stream);
+bchdav_status bchdav_destroy(bchdav_handle h);
+bchdav_status bchdav_set_stream(bchdav_handle h, void* cuda_stream);
+const char* bchdav_status_string(bchdav_status s);
+const char* bchdav_last_error(bchdav_handle h);   /* NULL handle: last create error */
+
+/* ---- Eq. (1): the symmetric normalized Laplacian ------------------------ */
+
+/* Build A = I - D^{-1/2} S D^{-1/2} from n_edges undirected edges
+ * (src[e], dst[e]) given as DEVICE int32 arrays.  Self loops are dropped,
+ * both orientations and repeats count once (S is 0/1).  Output is canonical
+ * CSR: columns ascending, diagonal stored explicitly as 1.0, off-diagonal
+ * -(r_i * r_j) with r_i = 1/sqrt(d_i) (IEEE), a degree-0 row holding only its
+ * diagonal; val_f32 is the round-to-nearest float of val.  The arrays of *out
+ * are allocated by the library and released with bchdav_free_csr.  Returns
+ * BCHDAV_ERR_ARG for an endpoint outside [0, n). */
+bchdav_status bchdav_build_laplacian(bchdav_handle h, int32_t n, int64_t n_edges,
+                                     const int32_t* src, const int32_t* dst, bchdav_csr* out);
+bchdav_status bchdav_free_csr(bchdav_handle h, bchdav_csr* csr);
+
+/* Copy the arrays of csr into caller-owned device arrays (n + 1 and nnz
+ * entries; val_f32 may be NULL to skip it), ordered on the handle's stream and
+ * complete when the call returns. */
+bchdav_status bchdav_copy_csr(bchdav_handle h, const bchdav_csr* csr, int32_t* rowptr,
+                              int32_t* colidx, double* val, float* val_f32);
+
+/* Check a caller-built CSR on the device (row pointers monotone, columns in
+ * range and strictly ascending per row).  BCHDAV_ERR_CSR when it is not. */
+bchdav_status bchdav_check_csr(bchdav_handle h, const bchdav_csr* A);
+
+/* ---- Algorithm 2 ---------------------------------------------------------- */
+
+/* k smallest eigenpairs of A by block Chebyshev-Davidson (Algorithm 2) with
+ * block size b (k_b), filter degree m, active-space limit act_max (0 = the
+ * default max(5b, 30)) and convergence tolerance tol on the relative residual
+ * ||A v - lambda v|| / ||v||.  evals: k doubles, ascending (device).  evecs:
+ * N x k row-major, ld = k (device).  info may be NULL.  Requires 1 <= k <= N,
+ * b >= 1, m >= 1, 2b <= act_max and max(dim_max, k + 2b) <= N.
+ * Returns BCHDAV_NOT_CONVERGED (with the pairs locked so far, sorted, in the
+ * leading info->n_converged slots) when itmax is reached. */
+bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int32_t b, int32_t m,
+                           int32_t act_max, double tol, const bchdav_opts* opts,
+                           double* evals, double* evecs, bchdav_info* info);
+
+/* Same as bchdav_solve with HOST arrays for the CSR, V_init and the results:
+ * copies in, solves, copies out, all inside the call (the end-to-end path). */
+bchdav_status bchdav_solve_host(bchdav_handle h, int32_t n, int64_t nnz, const int32_t* rowptr,
+                                const int32_t* colidx, const double* val, int32_t k, int32_t b,
+                                int32_t m, int32_t act_max, double tol, const bchdav_opts* opts,
+                                double* evals_host, double* evecs_host, bchdav_info* info);
+
+/* Per-iteration records of the last solve of this handle (opts.record_history). */
+int32_t bchdav_history(bchdav_handle h, bchdav_iter_record* out, int32_t max_records);
+
+/* ---- single steps (each is one step of Algorithm 2 / 3) -------------------- */
+
+/* Algorithm 3: Y = p_m(A) X with p_m(x) = T_m((x - c)/e) / T_m((a0 - c)/e),
+ * c = (a + upb)/2, e = (upb - a)/2, computed by the scaled three-term
+ * recurrence.  X, Y: N x b, leading dimensions ldx, ldy (distinct buffers).
+ * precision = BCHDAV_PREC_MIXED runs the recurrence in float32 (A->val_f32
+ * required); X and Y stay float64 and are rounded on entry / widened on exit. */
+bchdav_status bchdav_filter(bchdav_handle h, const bchdav_csr* A, const double* X, int32_t ldx,
+                            int32_t b, int32_t m, double a, double upb, double a0,
+                            int32_t precision, double* Y, int32_t ldy);
+
+/* Plain SpMM Y = A X (Eq. (6)), float64.  X: N x b (ldx), Y: N x b (ldy). */
+bchdav_status bchdav_spmm(bchdav_handle h, const bchdav_csr* A, const double* X, int32_t ldx,
+                          int32_t b, double* Y, int32_t ldy);
+
+/* Step 6: orthonormalise the N x b block X (in place, ldx) against the k
+ * orthonormal columns of V (ldv) and among themselves: two classical
+ * Gram-Schmidt passes against V, then column-by-column Gram-Schmidt with a
+ * second pass inside the block; a column whose remaining norm is <= tau_dep
+ * times its original norm (or zero) is replaced by Philox random vector
+ * number *rep_counter (seed, stream 1) and the block is redone.  *rep_counter
+ * is advanced by the number of replacements, *n_replaced receives it. */
+bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V, int32_t ldv,
+                                    int32_t k, double* X, int32_t ldx, int32_t b, uint64_t seed,
+                                    double tau_dep, int64_t* rep_counter, int32_t* n_replaced);
+
+/* Step 9: H Y = Y D for the symmetric n x n float64 matrix H (ld_h; only the
+ * upper triangle is read).  D: n eigenvalues ascending; Y: n x n, column j the
+ * eigenvector of D[j] (row-major, ld_y).  Householder tridiagonalisation and
+ * implicit-shift QL, all on the device. */
+bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t ld_h, double* D,
+                          double* Y, int32_t ld_y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCHDAV_H */

@@ -1,0 +1,337 @@
+"""GB300 (sm_103a) block Chebyshev-Davidson eigensolver for graph Laplacians.
+
+Thin ctypes binding over the C-ABI library ``libbchdav.so`` (declared in
+``include/bchdav.h``).  Every numerical step runs in the library's CUDA
+kernels; this module only marshals arguments.  PyTorch supplies device
+memory and the current CUDA stream.  Importing works without a GPU; any call
+that needs the library raises if it was not built or cannot be loaded (there is
+no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+__all__ = [
+    "lib", "build", "Handle", "DeviceCSR", "BchdavError", "SolveInfo", "IterRecord",
+    "PREC_FP64", "PREC_MIXED", "EXPORTED_SYMBOLS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libbchdav.so")
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+STATUS = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "invalid CSR",
+          -3: "out of device memory", -4: "CUDA error", -5: "non-finite value",
+          -6: "device wait timed out"}
+
+EXPORTED_SYMBOLS = [
+    "bchdav_create", "bchdav_destroy", "bchdav_set_stream", "bchdav_status_string",
+    "bchdav_last_error", "bchdav_build_laplacian", "bchdav_free_csr", "bchdav_copy_csr", "bchdav_check_csr",
+    "bchdav_solve", "bchdav_solve_host", "bchdav_history", "bchdav_filter", "bchdav_spmm",
+    "bchdav_orthonormalize", "bchdav_eigh",
+]
+
+
+class BchdavError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CSRStruct(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("colidx", C.c_void_p), ("val", C.c_void_p), ("val_f32", C.c_void_p)]
+
+
+class OptsStruct(C.Structure):
+    _fields_ = [("dim_max", C.c_int32), ("itmax", C.c_int32), ("precision", C.c_int32),
+                ("reserved0", C.c_int32), ("seed", C.c_uint64), ("v_init", C.c_void_p),
+                ("k_init", C.c_int32), ("ld_v_init", C.c_int32), ("record_history", C.c_int32),
+                ("reserved1", C.c_int32)]
+
+
+class InfoStruct(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("n_converged", C.c_int32), ("n_spmm", C.c_int32),
+                ("n_replaced", C.c_int32), ("max_rel_resid", C.c_double),
+                ("ms_total", C.c_double), ("ms_filter", C.c_double), ("ms_orth", C.c_double),
+                ("ms_spmm_w", C.c_double), ("ms_h", C.c_double), ("ms_eig", C.c_double),
+                ("ms_rot", C.c_double), ("ms_resid", C.c_double), ("ms_other", C.c_double),
+                ("filter_bytes", C.c_double), ("filter_ms_kernels", C.c_double),
+                ("n_kernel_launches", C.c_int64)]
+
+
+class IterStruct(C.Structure):
+    _fields_ = [("it", C.c_int32), ("k_c", C.c_int32), ("e_c", C.c_int32), ("k_act", C.c_int32),
+                ("k_sub", C.c_int32), ("k_old", C.c_int32), ("n_rep", C.c_int32),
+                ("k_orth", C.c_int32), ("low_nwb", C.c_double), ("max_resid", C.c_double)]
+
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from .build import build as _build
+    return _build(force=force, verbose=verbose)
+
+
+def lib() -> C.CDLL:
+    """Load libbchdav.so (building it first if sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from .build import needs_build
+    if needs_build():
+        build()
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"CUDA library missing: {_LIB_PATH}")
+    L = C.CDLL(_LIB_PATH)
+    i32, i64, u64, d, p = C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_void_p
+    sig = {
+        "bchdav_create": (i32, [C.POINTER(p), p]),
+        "bchdav_destroy": (i32, [p]),
+        "bchdav_set_stream": (i32, [p, p]),
+        "bchdav_status_string": (C.c_char_p, [i32]),
+        "bchdav_last_error": (C.c_char_p, [p]),
+        "bchdav_build_laplacian": (i32, [p, i32, i64, p, p, C.POINTER(CSRStruct)]),
+        "bchdav_free_csr": (i32, [p, C.POINTER(CSRStruct)]),
+        "bchdav_copy_csr": (i32, [p, C.POINTER(CSRStruct), p, p, p, p]),
+        "bchdav_check_csr": (i32, [p, C.POINTER(CSRStruct)]),
+        "bchdav_solve": (i32, [p, C.POINTER(CSRStruct), i32, i32, i32, i32, d,
+                               C.POINTER(OptsStruct), p, p, C.POINTER(InfoStruct)]),
+        "bchdav_solve_host": (i32, [p, i32, i64, p, p, p, i32, i32, i32, i32, d,
+                                    C.POINTER(OptsStruct), p, p, C.POINTER(InfoStruct)]),
+        "bchdav_history": (i32, [p, C.POINTER(IterStruct), i32]),
+        "bchdav_filter": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, i32, d, d, d, i32, p, i32]),
+        "bchdav_spmm": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, p, i32]),
+        "bchdav_orthonormalize": (i32, [p, i32, p, i32, i32, p, i32, i32, u64, d,
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+        "bchdav_eigh": (i32, [p, i32, p, i32, p, p, i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+@dataclass
+class DeviceCSR:
+    """The Laplacian in CSR form, held in torch CUDA tensors."""
+    n: int
+    rowptr: "object"   # int32 [n+1]
+    colidx: "object"   # int32 [nnz]
+    val: "object"      # float64 [nnz]
+    val_f32: "object" = None  # float32 [nnz] or None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    def struct(self) -> CSRStruct:
+        return CSRStruct(self.n, self.nnz, _ptr(self.rowptr), _ptr(self.colidx), _ptr(self.val),
+                         _ptr(self.val_f32))
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iters: int
+    n_converged: int
+    n_spmm: int
+    n_replaced: int
+    max_rel_resid: float
+    ms: dict
+    filter_bytes: float
+    filter_ms: float
+    launches: int
+
+
+@dataclass
+class IterRecord:
+    it: int
+    k_c: int
+    e_c: int
+    k_act: int
+    k_sub: int
+    k_old: int
+    n_rep: int
+    k_orth: int
+    low_nwb: float
+    max_resid: float
+
+
+class Handle:
+    """A library handle bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None):
+        import torch
+        self.L = lib()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._stream = int(stream)
+        h = C.c_void_p()
+        st = self.L.bchdav_create(C.byref(h), C.c_void_p(self._stream))
+        if st != 0:
+            raise BchdavError(st, self.L.bchdav_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.bchdav_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=(0,)):
+        if st not in allow:
+            raise BchdavError(st, self.L.bchdav_last_error(self.h).decode())
+        return st
+
+    def set_stream(self, stream):
+        self._stream = int(stream)
+        self._check(self.L.bchdav_set_stream(self.h, C.c_void_p(self._stream)))
+
+    # ---- Eq. (1)
+    def build_laplacian(self, n: int, src, dst) -> DeviceCSR:
+        """A = I - D^{-1/2} S D^{-1/2} from int32 CUDA edge tensors (library-built CSR)."""
+        import torch
+        cs = CSRStruct()
+        self._check(self.L.bchdav_build_laplacian(self.h, n, int(src.numel()), _ptr(src), _ptr(dst),
+                                                  C.byref(cs)))
+        nnz = int(cs.nnz)
+        dev = src.device
+        # copy into torch-owned tensors, then release the library's arrays
+        rowptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        colidx = torch.empty(nnz, dtype=torch.int32, device=dev)
+        val = torch.empty(nnz, dtype=torch.float64, device=dev)
+        val32 = torch.empty(nnz, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)
+        try:
+            self._check(self.L.bchdav_copy_csr(self.h, C.byref(cs), _ptr(rowptr), _ptr(colidx),
+                                               _ptr(val), _ptr(val32)))
+        finally:
+            self.L.bchdav_free_csr(self.h, C.byref(cs))
+        return DeviceCSR(n, rowptr, colidx, val, val32)
+
+    def check_csr(self, A: DeviceCSR):
+        cs = A.struct()
+        return self._check(self.L.bchdav_check_csr(self.h, C.byref(cs)), allow=(0, -2))
+
+    # ---- Algorithm 2
+    def solve(self, A: DeviceCSR, k: int, b: int, m: int, act_max: int, tol: float, *,
+              v_init=None, precision: int = PREC_FP64, dim_max: int = 0, itmax: int = 0,
+              seed: int = 0, record_history: bool = False, evals=None, evecs=None):
+        import torch
+        dev = A.rowptr.device
+        if evals is None:
+            evals = torch.zeros(k, dtype=torch.float64, device=dev)
+        if evecs is None:
+            evecs = torch.zeros((A.n, k), dtype=torch.float64, device=dev)
+        opts = OptsStruct()
+        opts.dim_max = dim_max
+        opts.itmax = itmax
+        opts.precision = precision
+        opts.seed = seed
+        opts.record_history = 1 if record_history else 0
+        if v_init is not None:
+            assert v_init.dtype == torch.float64 and v_init.is_cuda and v_init.stride(1) == 1
+            opts.v_init = _ptr(v_init)
+            opts.k_init = v_init.shape[1]
+            opts.ld_v_init = v_init.stride(0)
+        info = InfoStruct()
+        cs = A.struct()
+        st = self.L.bchdav_solve(self.h, C.byref(cs), k, b, m, act_max, tol, C.byref(opts),
+                                 _ptr(evals), _ptr(evecs), C.byref(info))
+        self._check(st, allow=(0, 1))
+        return evals, evecs, self._info(st, info)
+
+    def solve_host(self, n, rowptr, colidx, val, k, b, m, act_max, tol, *, precision=PREC_FP64,
+                   seed=0, evals=None, evecs=None, v_init=None):
+        """End-to-end call with host (numpy) arrays: copies in, solves, copies out."""
+        import numpy as np
+        if evals is None:
+            evals = np.zeros(k)
+        if evecs is None:
+            evecs = np.zeros((n, k))
+        opts = OptsStruct()
+        opts.precision = precision
+        opts.seed = seed
+        if v_init is not None:
+            v_init = np.ascontiguousarray(v_init, dtype=np.float64)
+            opts.v_init = v_init.ctypes.data
+            opts.k_init = v_init.shape[1]
+            opts.ld_v_init = v_init.shape[1]
+        info = InfoStruct()
+        st = self.L.bchdav_solve_host(self.h, n, int(colidx.shape[0]), rowptr.ctypes.data,
+                                      colidx.ctypes.data, val.ctypes.data, k, b, m, act_max, tol,
+                                      C.byref(opts), evals.ctypes.data, evecs.ctypes.data,
+                                      C.byref(info))
+        self._check(st, allow=(0, 1))
+        return evals, evecs, self._info(st, info)
+
+    def _info(self, st, info) -> SolveInfo:
+        ms = dict(total=info.ms_total, filter=info.ms_filter, orth=info.ms_orth,
+                  spmm_w=info.ms_spmm_w, h=info.ms_h, eig=info.ms_eig, rot=info.ms_rot,
+                  resid=info.ms_resid, other=info.ms_other)
+        return SolveInfo(st, info.iters, info.n_converged, info.n_spmm, info.n_replaced,
+                         info.max_rel_resid, ms, info.filter_bytes, info.filter_ms_kernels,
+                         info.n_kernel_launches)
+
+    def history(self):
+        n = self.L.bchdav_history(self.h, None, 0)
+        arr = (IterStruct * max(n, 1))()
+        self.L.bchdav_history(self.h, arr, n)
+        return [IterRecord(r.it, r.k_c, r.e_c, r.k_act, r.k_sub, r.k_old, r.n_rep, r.k_orth,
+                           r.low_nwb, r.max_resid) for r in arr[:n]]
+
+    # ---- single steps
+    def filter(self, A: DeviceCSR, X, m: int, a: float, upb: float, a0: float,
+               precision: int = PREC_FP64, Y=None):
+        import torch
+        if Y is None:
+            Y = torch.empty_like(X)
+        cs = A.struct()
+        self._check(self.L.bchdav_filter(self.h, C.byref(cs), _ptr(X), X.stride(0), X.shape[1], m,
+                                         a, upb, a0, precision, _ptr(Y), Y.stride(0)))
+        return Y
+
+    def spmm(self, A: DeviceCSR, X, Y=None):
+        import torch
+        if Y is None:
+            Y = torch.empty_like(X)
+        cs = A.struct()
+        self._check(self.L.bchdav_spmm(self.h, C.byref(cs), _ptr(X), X.stride(0), X.shape[1],
+                                       _ptr(Y), Y.stride(0)))
+        return Y
+
+    def orthonormalize(self, V, X, *, seed: int = 0, tau_dep: float = 1e-10, rep_counter: int = 0):
+        """In place on X; returns (n_replaced, new rep_counter)."""
+        k = 0 if V is None else V.shape[1]
+        rc = C.c_int64(rep_counter)
+        nr = C.c_int32(0)
+        self._check(self.L.bchdav_orthonormalize(
+            self.h, X.shape[0], _ptr(V), (V.stride(0) if V is not None else 1), k, _ptr(X),
+            X.stride(0), X.shape[1], seed, tau_dep, C.byref(rc), C.byref(nr)))
+        return nr.value, rc.value
+
+    def eigh(self, H):
+        import torch
+        n = H.shape[0]
+        D = torch.empty(n, dtype=torch.float64, device=H.device)
+        Y = torch.empty((n, n), dtype=torch.float64, device=H.device)
+        self._check(self.L.bchdav_eigh(self.h, n, _ptr(H), H.stride(0), _ptr(D), _ptr(Y),
+                                       Y.stride(0)))
+        return D, Y

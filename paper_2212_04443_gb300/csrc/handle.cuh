@@ -1,0 +1,77 @@
+// Handle state: stream, error text, grow-only device workspace.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+struct bchdav_handle_s {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = bchdav::kSMs;
+  std::string err;
+  std::vector<DevBuf*> owned;
+  // workspace slots
+  DevBuf V, W, Vtmp, Xo, F[4], H, G, Y, D, part, eigw, small, norm0, val32, R;
+  DevBuf hrow, hcol, hval, hvinit, hev, hevec;   // device copies for bchdav_solve_host
+  DevBuf Rres, mix;   // mixed path: residual block of Step 12, per-column filter coefficients
+  std::vector<bchdav_iter_record> history;
+  double* host_pinned = nullptr;   // small pinned staging area
+  size_t host_pinned_doubles = 0;
+
+  void set_error(bchdav_status, const std::string& m) { err = m; }
+
+  bchdav_status ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return BCHDAV_OK;
+    b.release();
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      err = std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
+            cudaGetErrorString(e);
+      return BCHDAV_ERR_OOM;
+    }
+    b.bytes = bytes;
+    return BCHDAV_OK;
+  }
+
+  bchdav_status ensure_pinned(size_t doubles) {
+    if (host_pinned_doubles >= doubles) return BCHDAV_OK;
+    if (host_pinned) cudaFreeHost(host_pinned);
+    host_pinned = nullptr;
+    cudaError_t e = cudaMallocHost(&host_pinned, doubles * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      err = "pinned host allocation failed";
+      host_pinned_doubles = 0;
+      return BCHDAV_ERR_OOM;
+    }
+    host_pinned_doubles = doubles;
+    return BCHDAV_OK;
+  }
+
+  void release_all() {
+    DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
+                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix};
+    for (DevBuf* b : all) b->release();
+    if (host_pinned) cudaFreeHost(host_pinned);
+    host_pinned = nullptr;
+    host_pinned_doubles = 0;
+  }
+};

@@ -1,0 +1,89 @@
+// Launchers of the device kernels (one translation unit per family).
+#pragma once
+#include "common.cuh"
+
+namespace bchdav {
+
+// ---------------- SpMM family (spmm.cu) ----------------
+// Y = alpha * (A X) + beta * X + gamma * Z + diag(delta) R, row by row (Eq. (6)
+// with the epilogue of Algorithm 3).  Z may be NULL (gamma ignored); R may be
+// NULL (delta, one coefficient per column on the device, ignored).
+template <typename T>
+cudaError_t launch_spmm_axpby(cudaStream_t st, int n, const int* rowptr, const int* colidx,
+                              const T* val, const T* X, int ldx, int b, T* Y, int ldy,
+                              const T* Z, int ldz, T alpha, T beta, T gamma,
+                              const T* R = nullptr, int ldr = 0, const T* delta = nullptr);
+
+// Residual of Step 12: for column j, r_j = (A V)_j - d_j V_j; writes per-CTA
+// partial sums of r_j^2 and v_j^2 to partial[cta * 2b + {j, b + j}] and
+// returns the CTA count in *n_parts.  The vectors r_j are stored in Rout
+// (ld ldr) when it is not NULL.
+cudaError_t launch_spmm_resid(cudaStream_t st, int n, const int* rowptr, const int* colidx,
+                              const double* val, const double* V, int ldv, int b,
+                              const double* d, double* partial, int* n_parts,
+                              double* Rout = nullptr, int ldr = 0);
+int spmm_resid_max_parts(int n, int b);
+
+// ---------------- dense family (dense.cu) ----------------
+// partial[c] = A(rows of chunk c, 0:ka)^T B(rows of chunk c, 0:kb); ka*kb outputs.
+cudaError_t launch_gemm_tn_partial(cudaStream_t st, int n, const double* A, int lda, int ka,
+                                   const double* B, int ldb, int kb, double* partial,
+                                   int n_chunks);
+int gemm_tn_chunks(int n);
+// out[i] = scale * sum_c partial[c * count + i] (fixed order).
+cudaError_t launch_reduce_partials(cudaStream_t st, const double* partial, int n_chunks, int count,
+                                   double* out, double scale);
+// C(:, 0:nb) -= A(:, 0:k) B (k x nb, ldb) ; A and C distinct.
+cudaError_t launch_gemm_nn_sub(cudaStream_t st, int n, const double* A, int lda, int k,
+                               const double* B, int ldb, int nb, double* C, int ldc);
+// A(:, 0:nb) = A(:, 0:k) B  in place (nb <= k), row tiles staged in shared memory.
+cudaError_t launch_gemm_nn_inplace(cudaStream_t st, int n, double* A, int lda, int k,
+                                   const double* B, int ldb, int nb);
+// Column sums of squares of X (N x b): per-CTA partials, count b.
+cudaError_t launch_col_sumsq_partial(cudaStream_t st, int n, const double* X, int ldx, int b,
+                                     double* partial, int n_chunks);
+cudaError_t launch_copy_block(cudaStream_t st, int n, int w, const double* src, int lds,
+                              double* dst, int ldd);
+// dst(:, j) = src(:, perm[j]) for j < w (perm on the device).
+// X(:, 0:count) = X(:, shift:shift+count) in place (warp per row, chunked left to right).
+cudaError_t launch_shift_cols_left(cudaStream_t st, int n, double* X, int ldx, int count, int shift);
+cudaError_t launch_gather_cols(cudaStream_t st, int n, int w, const double* src, int lds,
+                               const int* perm, double* dst, int ldd);
+cudaError_t launch_f64_to_f32(cudaStream_t st, int n, int w, const double* src, int lds,
+                              float* dst, int ldd);
+cudaError_t launch_f32_to_f64(cudaStream_t st, int n, int w, const float* src, int lds,
+                              double* dst, int ldd);
+// Mixed-precision filter inputs: column j of Z0/R32 (float, ldo) takes
+// float(X(:, j)) / 0 when src[j] < 0, else 0 / float(R(:, src[j])).
+cudaError_t launch_mixed_inputs(cudaStream_t st, int n, int b, const double* X, int ldx,
+                                const double* R, int ldr, const int* src, float* Z0, float* R32,
+                                int ldo);
+cudaError_t launch_f64_to_f32_vec(cudaStream_t st, long long count, const double* src, float* dst);
+// Column `col` of X := Philox random vector `vec` of `stream`.
+cudaError_t launch_fill_random_col(cudaStream_t st, int n, double* X, int ldx, int col,
+                                   uint64_t seed, uint32_t stream, uint32_t vec);
+// H(0:k_act, k_act-b:k_act) = G (k_act x b), mirrored, new diagonal block symmetrised.
+cudaError_t launch_h_update(cudaStream_t st, double* H, int ldh, const double* G, int k_act, int b);
+// H = diag(d[0:k]) (ldh x ldh cleared up to k).
+cudaError_t launch_h_diag(cudaStream_t st, double* H, int ldh, const double* d, int k, int clear);
+// Non-finite check: flag |= any(!isfinite(x)).
+cudaError_t launch_check_finite(cudaStream_t st, int n, int w, const double* X, int ldx, int* flag);
+
+// ---------------- orthonormalisation (orth.cu) ----------------
+// Column-by-column classical Gram-Schmidt with two passes inside the block,
+// starting at column j0; stops at the first column found dependent and
+// reports it in *dep (-1 if none).  Cooperative launch.
+cudaError_t launch_inblock_gs(cudaStream_t st, int n, double* X, int ldx, int b, int j0,
+                              const double* norm0, double tau_dep, double* scratch, int* dep,
+                              double* final_norms);
+size_t inblock_gs_scratch_doubles(int b);
+
+// ---------------- eigensolver (eig.cu) ----------------
+// Symmetric eigendecomposition of the n x n matrix H (upper triangle read).
+cudaError_t launch_eigh(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
+                        int ldy, double* work, int* status);
+size_t eigh_work_doubles(int n);
+
+// ---------------- Laplacian assembly (laplacian.cu) ----------------
+struct LapWork;
+}  // namespace bchdav

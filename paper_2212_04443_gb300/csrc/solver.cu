@@ -1,0 +1,836 @@
+// C-ABI entry points and the device-resident driver of Algorithm 2 (block
+// Chebyshev-Davidson with inner-outer restart).  Every vector and matrix of
+// the iteration lives in device memory; per outer iteration the host reads
+// back only the k_act Ritz values and the k_b residual norms it needs for the
+// control decisions of Steps 10-18.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "handle.cuh"
+#include "kernels.cuh"
+
+using namespace bchdav;
+
+namespace {
+
+std::string g_create_error;
+
+constexpr double kTauDepF64 = 1e-10;
+constexpr double kTauDepMixed = 1e-10;
+constexpr double kLowNwbEps = 1e-12;
+
+#define HCUDA(expr) BCHDAV_CUDA_OK(expr, h)
+
+bchdav_status check_csr_args(bchdav_handle h, const bchdav_csr* A) {
+  if (!A || A->n <= 0 || !A->rowptr || !A->colidx || !A->val || A->nnz < A->n ||
+      A->nnz >= (int64_t)INT32_MAX) {
+    h->set_error(BCHDAV_ERR_ARG, "invalid CSR descriptor");
+    return BCHDAV_ERR_ARG;
+  }
+  return BCHDAV_OK;
+}
+
+// ---------------- timing helper ----------------
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  double acc = 0.0;
+  bool pending = false;
+  void init() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  void destroy() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  void start(cudaStream_t s) { cudaEventRecord(a, s); }
+  void stop(cudaStream_t s) {
+    cudaEventRecord(b, s);
+    pending = true;
+  }
+  void collect() {   // after a stream sync
+    if (!pending) return;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) acc += ms;
+    pending = false;
+  }
+};
+
+// ---------------- Algorithm 3 ----------------
+// Y = p_m(A) X.  prec MIXED: recurrence in float32 (val32 required).
+bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val32, const double* X,
+                         int ldx, int b, int m, double a, double upb, double a0, int prec,
+                         double* Y, int ldy, double* bytes_out) {
+  const int n = A->n;
+  cudaStream_t st = h->stream;
+  const double c = (a + upb) / 2.0, e = (upb - a) / 2.0;
+  double sigma = e / (a0 - c);
+  const double tau = 2.0 / sigma;
+  const size_t sx = prec == BCHDAV_PREC_MIXED ? 4 : 8;
+  const int ldb = prec == BCHDAV_PREC_MIXED ? round_up(b, 4) : round_up(b, 2);
+  for (int i = 0; i < 4; ++i) BCHDAV_TRY(h->ensure(h->F[i], (size_t)n * ldb * sx));
+  double bytes = 0.0;
+  const double csr_bytes = 4.0 * (n + 1) + (double)A->nnz * (4.0 + (double)sx);
+  if (prec == BCHDAV_PREC_MIXED) {
+    float* T[4] = {h->F[0].as<float>(), h->F[1].as<float>(), h->F[2].as<float>(),
+                   h->F[3].as<float>()};
+    HCUDA(launch_f64_to_f32(st, n, b, X, ldx, T[0], ldb));
+    // step 1: U = (A X - c X) sigma / e
+    HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[0], ldb, b, T[1], ldb,
+                                   nullptr, 0, (float)(sigma / e), (float)(-c * sigma / e), 0.f));
+    bytes += csr_bytes + 3.0 * n * b * sx;
+    int prev = 0, cur = 1;
+    for (int i = 2; i <= m; ++i) {
+      double sigma1 = 1.0 / (tau - sigma);
+      int nxt = 0;
+      while (nxt == prev || nxt == cur) ++nxt;
+      HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[cur], ldb, b, T[nxt],
+                                     ldb, T[prev], ldb, (float)(2.0 * sigma1 / e),
+                                     (float)(-2.0 * sigma1 * c / e), (float)(-sigma * sigma1)));
+      bytes += csr_bytes + 4.0 * n * b * sx;
+      prev = cur;
+      cur = nxt;
+      sigma = sigma1;
+    }
+    HCUDA(launch_f32_to_f64(st, n, b, T[cur], ldb, Y, ldy));
+  } else {
+    double* T[4] = {h->F[0].as<double>(), h->F[1].as<double>(), h->F[2].as<double>(),
+                    h->F[3].as<double>()};
+    const double* prevp = X;
+    int prevld = ldx;
+    double* out = (m == 1) ? Y : T[0];
+    int outld = (m == 1) ? ldy : ldb;
+    HCUDA(launch_spmm_axpby<double>(st, n, A->rowptr, A->colidx, A->val, X, ldx, b, out, outld,
+                                    nullptr, 0, sigma / e, -c * sigma / e, 0.0));
+    bytes += csr_bytes + 3.0 * n * b * sx;
+    const double* curp = out;
+    int curld = outld;
+    int slot = 1;
+    for (int i = 2; i <= m; ++i) {
+      double sigma1 = 1.0 / (tau - sigma);
+      double* nxt;
+      int nxtld;
+      if (i == m) {
+        nxt = Y;
+        nxtld = ldy;
+      } else {
+        nxt = T[slot % 3];
+        nxtld = ldb;
+        ++slot;
+      }
+      HCUDA(launch_spmm_axpby<double>(st, n, A->rowptr, A->colidx, A->val, curp, curld, b, nxt,
+                                      nxtld, prevp, prevld, 2.0 * sigma1 / e,
+                                      -2.0 * sigma1 * c / e, -sigma * sigma1));
+      bytes += csr_bytes + 4.0 * n * b * sx;
+      prevp = curp;
+      prevld = curld;
+      curp = nxt;
+      curld = nxtld;
+      sigma = sigma1;
+    }
+  }
+  if (bytes_out) *bytes_out += bytes;
+  return BCHDAV_OK;
+}
+
+// Mixed-precision filter of Step 5.  Column j is either a plain column
+// (theta[j] is NaN): float32 recurrence of Algorithm 3 on X(:, j); or the
+// residual r_j = A u_j - theta_j u_j of a Ritz pair (theta_j finite): the
+// float32 recurrence applies s(x) = (p(x) - p(theta_j)) / (x - theta_j) to r_j,
+//   Z_1 = (sigma_1 / e) r,
+//   Z_{k+1} = (2 sigma_{k+1} / e) ((A - c) Z_k + p_k(theta) r) - sigma_k sigma_{k+1} Z_{k-1},
+// since p(A) u_j = p(theta_j) u_j + s(A) r_j with u_j in the basis, both give
+// the same vector after orthogonalisation against the basis (Step 6), and the
+// float32 rounding is relative to ||s(A) r_j|| instead of ||p(A) u_j||.
+bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float* val32,
+                               const double* X, int ldx, const double* R, int ldr,
+                               const int* src_host, const double* theta, int b, int m, double a,
+                               double upb, double a0, double* Y, int ldy, double* bytes_out) {
+  const int n = A->n;
+  cudaStream_t st = h->stream;
+  const double c = (a + upb) / 2.0, e = (upb - a) / 2.0;
+  const double sigma1 = e / (a0 - c);
+  const double tau = 2.0 / sigma1;
+  const int ldb = round_up(b, 4);
+  for (int i = 0; i < 4; ++i) BCHDAV_TRY(h->ensure(h->F[i], (size_t)n * ldb * sizeof(float)));
+  BCHDAV_TRY(h->ensure(h->Rres, (size_t)n * round_up(b, 2) * sizeof(double)));
+  float* T[4] = {h->F[0].as<float>(), h->F[1].as<float>(), h->F[2].as<float>(),
+                 h->F[3].as<float>()};
+  // R32 lives in the fourth float buffer's twin: reuse mix buffer for coefficients
+  BCHDAV_TRY(h->ensure(h->mix, (size_t)(m + 1) * 64 * sizeof(float) + 64 * sizeof(int) +
+                                   (size_t)n * ldb * sizeof(float) + 256));
+  int* src_d = reinterpret_cast<int*>(h->mix.p);
+  float* delta_d = reinterpret_cast<float*>(h->mix.as<char>() + 64 * sizeof(int));
+  float* R32 = reinterpret_cast<float*>(
+      h->mix.as<char>() + 64 * sizeof(int) + (size_t)(m + 1) * 64 * sizeof(float));
+  // host: sigma sequence, p_k(theta_j), deltas
+  BCHDAV_TRY(h->ensure_pinned((size_t)(m + 1) * 64 + 128));
+  float* dh = reinterpret_cast<float*>(h->host_pinned);
+  int* sh = reinterpret_cast<int*>(h->host_pinned + (size_t)(m + 1) * 32 + 32);
+  bool any_res = false;
+  std::vector<double> pkm1(b, 1.0), pk(b, 0.0);
+  for (int j = 0; j < b; ++j) {
+    bool res = src_host[j] >= 0;
+    any_res = any_res || res;
+    sh[j] = src_host[j];
+    pk[j] = res ? sigma1 * (theta[j] - c) / e : 0.0;   // p_1(theta)
+    dh[j] = res ? (float)(sigma1 / e) : 0.f;            // step 1 coefficient
+  }
+  std::vector<double> sig(m + 1);
+  sig[1] = sigma1;
+  for (int i = 2; i <= m; ++i) {
+    sig[i] = 1.0 / (tau - sig[i - 1]);
+    for (int j = 0; j < b; ++j) {
+      bool res = src_host[j] >= 0;
+      // coefficient of r in step i uses p_{i-1}(theta)
+      dh[(size_t)(i - 1) * 64 + j] = res ? (float)(2.0 * sig[i] / e * pk[j]) : 0.f;
+      double pnew = res ? (2.0 * sig[i] / e * (theta[j] - c) * pk[j] - sig[i - 1] * sig[i] * pkm1[j])
+                        : 0.0;
+      pkm1[j] = pk[j];
+      pk[j] = pnew;
+    }
+  }
+  HCUDA(cudaMemcpyAsync(src_d, sh, b * sizeof(int), cudaMemcpyHostToDevice, st));
+  HCUDA(cudaMemcpyAsync(delta_d, dh, (size_t)m * 64 * sizeof(float), cudaMemcpyHostToDevice, st));
+  HCUDA(launch_mixed_inputs(st, n, b, X, ldx, any_res ? R : X, any_res ? ldr : ldx, src_d, T[0],
+                            R32, ldb));
+  const float* Rp = any_res ? R32 : nullptr;
+  const double csr_bytes = 4.0 * (n + 1) + (double)A->nnz * 8.0;
+  double bytes = 0.0;
+  HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[0], ldb, b, T[1], ldb,
+                                 nullptr, 0, (float)(sigma1 / e), (float)(-c * sigma1 / e), 0.f, Rp,
+                                 ldb, delta_d));
+  bytes += csr_bytes + (any_res ? 4.0 : 3.0) * n * b * 4.0;
+  int prev = 0, cur = 1;
+  for (int i = 2; i <= m; ++i) {
+    int nxt = 0;
+    while (nxt == prev || nxt == cur) ++nxt;
+    HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[cur], ldb, b, T[nxt], ldb,
+                                   T[prev], ldb, (float)(2.0 * sig[i] / e),
+                                   (float)(-2.0 * sig[i] * c / e), (float)(-sig[i - 1] * sig[i]),
+                                   Rp, ldb, delta_d + (size_t)(i - 1) * 64));
+    bytes += csr_bytes + (any_res ? 5.0 : 4.0) * n * b * 4.0;
+    prev = cur;
+    cur = nxt;
+  }
+  HCUDA(launch_f32_to_f64(st, n, b, T[cur], ldb, Y, ldy));
+  if (bytes_out) *bytes_out += bytes;
+  return BCHDAV_OK;
+}
+
+// ---------------- Step 6 ----------------
+bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, double* X, int ldx,
+                       int b, uint64_t seed, double tau_dep, int64_t* rep_counter, int* n_rep) {
+  cudaStream_t st = h->stream;
+  if (b > 64) {
+    h->set_error(BCHDAV_ERR_ARG, "block size b must be <= 64");
+    return BCHDAV_ERR_ARG;
+  }
+  const int chunks = gemm_tn_chunks(n);
+  const int ka_max = std::max(k, 1);
+  const size_t part_doubles = std::max((size_t)chunks * ka_max * b, (size_t)chunks * b);
+  BCHDAV_TRY(h->ensure(h->part, part_doubles * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->G, (size_t)std::max(ka_max * b, 64) * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->norm0, (size_t)(3 * 64 + 16) * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->small, inblock_gs_scratch_doubles(b) * sizeof(double) + 64));
+  BCHDAV_TRY(h->ensure_pinned(256));
+  double* norm0_d = h->norm0.as<double>();
+  double* fin_d = norm0_d + 64;
+  int* dep_d = reinterpret_cast<int*>(norm0_d + 128);
+  double* hp = h->host_pinned;
+
+  auto col_norms = [&](double* out_host) -> bchdav_status {
+    int nc = std::min(chunks, ceil_div(n, 256 / b));
+    HCUDA(launch_col_sumsq_partial(st, n, X, ldx, b, h->part.as<double>(), nc));
+    HCUDA(launch_reduce_partials(st, h->part.as<double>(), nc, b, h->G.as<double>(), 1.0));
+    HCUDA(cudaMemcpyAsync(hp, h->G.as<double>(), b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HCUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < b; ++j) out_host[j] = std::sqrt(hp[j]);
+    return BCHDAV_OK;
+  };
+
+  std::vector<double> norm0(b);
+  BCHDAV_TRY(col_norms(norm0.data()));
+  *n_rep = 0;
+  for (int attempt = 0; attempt < b + 16; ++attempt) {
+    if (k > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        HCUDA(launch_gemm_tn_partial(st, n, V, ldv, k, X, ldx, b, h->part.as<double>(), chunks));
+        HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k * b, h->G.as<double>(), 1.0));
+        HCUDA(launch_gemm_nn_sub(st, n, V, ldv, k, h->G.as<double>(), b, b, X, ldx));
+      }
+    }
+    for (int j = 0; j < b; ++j) hp[j] = norm0[j];
+    reinterpret_cast<int*>(hp + 64)[0] = -1;
+    HCUDA(cudaMemcpyAsync(norm0_d, hp, b * sizeof(double), cudaMemcpyHostToDevice, st));
+    HCUDA(cudaMemcpyAsync(dep_d, hp + 64, sizeof(int), cudaMemcpyHostToDevice, st));
+    HCUDA(launch_inblock_gs(st, n, X, ldx, b, 0, norm0_d, tau_dep, h->small.as<double>(), dep_d,
+                            fin_d));
+    HCUDA(cudaMemcpyAsync(hp + 64, dep_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HCUDA(cudaStreamSynchronize(st));
+    const int dep = reinterpret_cast<int*>(hp + 64)[0];
+    if (dep < 0) return BCHDAV_OK;
+    HCUDA(launch_fill_random_col(st, n, X, ldx, dep, seed, kStreamReplace,
+                                 (uint32_t)(*rep_counter)));
+    ++(*rep_counter);
+    ++(*n_rep);
+    std::vector<double> nn(b);
+    BCHDAV_TRY(col_norms(nn.data()));
+    for (int j = 0; j < dep; ++j) norm0[j] = 1.0;
+    norm0[dep] = nn[dep];
+  }
+  h->set_error(BCHDAV_ERR_NONFINITE, "orthonormalisation: replacement vectors keep failing");
+  return BCHDAV_ERR_NONFINITE;
+}
+
+double median_of(std::vector<double> v) {
+  std::sort(v.begin(), v.end());
+  size_t n = v.size();
+  if (n % 2 == 1) return v[n / 2];
+  return 0.5 * (v[n / 2 - 1] + v[n / 2]);
+}
+
+}  // namespace
+
+// =====================================================================
+extern "C" {
+
+const char* bchdav_status_string(bchdav_status s) {
+  switch (s) {
+    case BCHDAV_OK: return "ok";
+    case BCHDAV_NOT_CONVERGED: return "not converged (itmax reached)";
+    case BCHDAV_ERR_ARG: return "invalid argument";
+    case BCHDAV_ERR_CSR: return "invalid CSR matrix";
+    case BCHDAV_ERR_OOM: return "out of device memory";
+    case BCHDAV_ERR_CUDA: return "CUDA error";
+    case BCHDAV_ERR_NONFINITE: return "non-finite value in the iteration";
+    case BCHDAV_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+bchdav_status bchdav_create(bchdav_handle* out, void* stream) {
+  if (!out) return BCHDAV_ERR_ARG;
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return BCHDAV_ERR_CUDA;
+  }
+  bchdav_handle h = new bchdav_handle_s();
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->device = dev;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  *out = h;
+  return BCHDAV_OK;
+}
+
+bchdav_status bchdav_destroy(bchdav_handle h) {
+  if (!h) return BCHDAV_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  h->release_all();
+  delete h;
+  return BCHDAV_OK;
+}
+
+bchdav_status bchdav_set_stream(bchdav_handle h, void* stream) {
+  if (!h) return BCHDAV_ERR_ARG;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return BCHDAV_OK;
+}
+
+const char* bchdav_last_error(bchdav_handle h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+int32_t bchdav_history(bchdav_handle h, bchdav_iter_record* out, int32_t max_records) {
+  if (!h) return 0;
+  int32_t n = (int32_t)h->history.size();
+  if (out && max_records > 0) {
+    int32_t c = std::min(n, max_records);
+    std::memcpy(out, h->history.data(), c * sizeof(bchdav_iter_record));
+  }
+  return n;
+}
+
+bchdav_status bchdav_spmm(bchdav_handle h, const bchdav_csr* A, const double* X, int32_t ldx,
+                          int32_t b, double* Y, int32_t ldy) {
+  if (!h) return BCHDAV_ERR_ARG;
+  BCHDAV_TRY(check_csr_args(h, A));
+  if (b < 1 || ldx < b || ldy < b || !X || !Y) {
+    h->set_error(BCHDAV_ERR_ARG, "spmm: bad block arguments");
+    return BCHDAV_ERR_ARG;
+  }
+  HCUDA(launch_spmm_axpby<double>(h->stream, A->n, A->rowptr, A->colidx, A->val, X, ldx, b, Y, ldy,
+                                  nullptr, 0, 1.0, 0.0, 0.0));
+  return BCHDAV_OK;
+}
+
+bchdav_status bchdav_filter(bchdav_handle h, const bchdav_csr* A, const double* X, int32_t ldx,
+                            int32_t b, int32_t m, double a, double upb, double a0,
+                            int32_t precision, double* Y, int32_t ldy) {
+  if (!h) return BCHDAV_ERR_ARG;
+  BCHDAV_TRY(check_csr_args(h, A));
+  if (b < 1 || m < 1 || ldx < b || ldy < b || !X || !Y || X == Y || !(upb > a) || !(a0 < a)) {
+    h->set_error(BCHDAV_ERR_ARG, "filter: bad arguments (need a0 < a < upb, m >= 1)");
+    return BCHDAV_ERR_ARG;
+  }
+  const float* v32 = A->val_f32;
+  if (precision == BCHDAV_PREC_MIXED && !v32) {
+    BCHDAV_TRY(h->ensure(h->val32, (size_t)A->nnz * sizeof(float)));
+    HCUDA(launch_f64_to_f32_vec(h->stream, A->nnz, A->val, h->val32.as<float>()));
+    v32 = h->val32.as<float>();
+  }
+  return run_filter(h, A, v32, X, ldx, b, m, a, upb, a0, precision, Y, ldy, nullptr);
+}
+
+bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V, int32_t ldv,
+                                    int32_t k, double* X, int32_t ldx, int32_t b, uint64_t seed,
+                                    double tau_dep, int64_t* rep_counter, int32_t* n_replaced) {
+  if (!h) return BCHDAV_ERR_ARG;
+  if (n < 1 || b < 1 || b > 64 || k < 0 || k + b > n || ldx < b || (k > 0 && (!V || ldv < k)) ||
+      !X || !rep_counter) {
+    h->set_error(BCHDAV_ERR_ARG, "orthonormalize: bad arguments");
+    return BCHDAV_ERR_ARG;
+  }
+  if (k > 768) {
+    h->set_error(BCHDAV_ERR_ARG, "orthonormalize: basis wider than supported (768)");
+    return BCHDAV_ERR_ARG;
+  }
+  int nr = 0;
+  bchdav_status s = run_orth(h, n, V, ldv, k, X, ldx, b, seed, tau_dep, rep_counter, &nr);
+  if (n_replaced) *n_replaced = nr;
+  return s;
+}
+
+bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t ld_h, double* D,
+                          double* Y, int32_t ld_y) {
+  if (!h) return BCHDAV_ERR_ARG;
+  if (n < 1 || n > 4096 || ld_h < n || ld_y < n || !H || !D || !Y) {
+    h->set_error(BCHDAV_ERR_ARG, "eigh: bad arguments");
+    return BCHDAV_ERR_ARG;
+  }
+  BCHDAV_TRY(h->ensure(h->eigw, eigh_work_doubles(n) * sizeof(double) + 64));
+  int* status_d = reinterpret_cast<int*>(h->eigw.as<char>() + eigh_work_doubles(n) * sizeof(double));
+  HCUDA(launch_eigh(h->stream, n, H, ld_h, D, Y, ld_y, h->eigw.as<double>(), status_d));
+  int st = 0;
+  HCUDA(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  HCUDA(cudaStreamSynchronize(h->stream));
+  if (st != 0) {
+    h->set_error(BCHDAV_ERR_NONFINITE, "eigh: QL iteration did not converge");
+    return BCHDAV_ERR_NONFINITE;
+  }
+  return BCHDAV_OK;
+}
+
+// ---------------------------------------------------------------------
+bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int32_t b, int32_t m,
+                           int32_t act_max_in, double tol, const bchdav_opts* opts_in,
+                           double* evals, double* evecs, bchdav_info* info) {
+  if (!h) return BCHDAV_ERR_ARG;
+  BCHDAV_TRY(check_csr_args(h, A));
+  bchdav_opts opts;
+  std::memset(&opts, 0, sizeof(opts));
+  if (opts_in) opts = *opts_in;
+  const int N = A->n;
+  const int act_max = act_max_in > 0 ? act_max_in : std::max(5 * b, 30);
+  int dim_max = opts.dim_max > 0 ? opts.dim_max : std::min(std::max(act_max + 2 * b, k + 30), N);
+  const int itmax = opts.itmax > 0 ? opts.itmax : 1000;
+  const int prec = opts.precision;
+  if (k < 1 || k > N || b < 1 || b > 64 || m < 1 || act_max < 2 * b || act_max > N ||
+      !(tol > 0) || !evals || !evecs || (prec != BCHDAV_PREC_FP64 && prec != BCHDAV_PREC_MIXED) ||
+      (opts.k_init > 0 && (!opts.v_init || opts.ld_v_init < opts.k_init))) {
+    h->set_error(BCHDAV_ERR_ARG, "solve: invalid k, b, m, act_max, tol or options");
+    return BCHDAV_ERR_ARG;
+  }
+  const int ncols = std::max(dim_max, k + 2 * b);
+  if (ncols > N || dim_max < act_max) {
+    h->set_error(BCHDAV_ERR_ARG, "solve: subspace (dim_max, k + 2b) larger than N or below act_max");
+    return BCHDAV_ERR_ARG;
+  }
+  if (act_max > 768 || ncols > 768) {
+    h->set_error(BCHDAV_ERR_ARG, "solve: act_max and dim_max are limited to 768");
+    return BCHDAV_ERR_ARG;
+  }
+  const int k_ri = std::max(act_max / 2, act_max - 3 * b);
+  cudaStream_t st = h->stream;
+  const double tau_dep = prec == BCHDAV_PREC_MIXED ? kTauDepMixed : kTauDepF64;
+
+  // ---- workspace
+  const int ldv = round_up(ncols, 2), ldw = round_up(act_max, 2), ldb = round_up(b, 2);
+  BCHDAV_TRY(h->ensure(h->V, (size_t)N * ldv * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->W, (size_t)N * ldw * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->Vtmp, (size_t)N * ldb * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->Xo, (size_t)N * ldb * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->R, (size_t)N * ldb * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->H, (size_t)act_max * act_max * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->Y, (size_t)act_max * act_max * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->D, (size_t)(act_max + 256 + ncols + 64) * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->eigw, eigh_work_doubles(act_max) * sizeof(double) + 64));
+  const int chunks = gemm_tn_chunks(N);
+  const int rparts = spmm_resid_max_parts(N, b);
+  BCHDAV_TRY(h->ensure(h->part, std::max((size_t)chunks * ncols * b,
+                                          (size_t)std::max(rparts, chunks) * 2 * 64) *
+                                    sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->G, (size_t)std::max(ncols * b, 64) * sizeof(double)));
+  BCHDAV_TRY(h->ensure_pinned((size_t)std::max(std::max(4 * act_max + 4 * ncols, 1024),
+                                                (m + 1) * 64 + 256)));
+  const float* val32 = A->val_f32;
+  if (prec == BCHDAV_PREC_MIXED && !val32) {
+    BCHDAV_TRY(h->ensure(h->val32, (size_t)A->nnz * sizeof(float)));
+    HCUDA(launch_f64_to_f32_vec(st, A->nnz, A->val, h->val32.as<float>()));
+    val32 = h->val32.as<float>();
+  }
+  double* V = h->V.as<double>();
+  double* W = h->W.as<double>();
+  double* Vtmp = h->Vtmp.as<double>();
+  double* Xo = h->Xo.as<double>();
+  double* Hm = h->H.as<double>();
+  double* Ym = h->Y.as<double>();
+  double* Dd = h->D.as<double>();            // act_max Ritz values
+  double* dsel = Dd + act_max;               // device staging for small vectors (256)
+  int* perm_d = reinterpret_cast<int*>(dsel + 256);   // ncols column indices
+  int* eig_status = reinterpret_cast<int*>(h->eigw.as<char>() +
+                                           eigh_work_doubles(act_max) * sizeof(double));
+  double* hp = h->host_pinned;
+  h->history.clear();
+
+  Timer tm_total, tm_filter, tm_orth, tm_spmm, tm_h, tm_eig, tm_rot, tm_res;
+  Timer* timers[] = {&tm_total, &tm_filter, &tm_orth, &tm_spmm, &tm_h, &tm_eig, &tm_rot, &tm_res};
+  for (Timer* t : timers) t->init();
+  struct Cleanup {
+    Timer** t;
+    int n;
+    ~Cleanup() {
+      for (int i = 0; i < n; ++i) t[i]->destroy();
+    }
+  } cleanup{timers, 8};
+  auto collect = [&]() {
+    for (Timer* t : timers)
+      if (t != &tm_total) t->collect();
+  };
+  double filter_bytes = 0.0;
+  const unsigned long long launches0 = __atomic_load_n(&bchdav::g_launches, __ATOMIC_RELAXED);
+  tm_total.start(st);
+
+  // ---- Step 1: bounds
+  const double lowb = 0.0, upperb = 2.0;
+  double low_nwb = lowb + (upperb - lowb) * (double)k / (double)N;
+
+  // ---- Step 2: first filter input
+  const int k_init = opts.k_init > 0 ? opts.k_init : 0;
+  const int n_first = std::min(b, k_init);
+  if (n_first > 0) HCUDA(launch_copy_block(st, N, n_first, opts.v_init, opts.ld_v_init, Vtmp, ldb));
+  uint32_t fill_counter = 0;
+  for (int j = n_first; j < b; ++j)
+    HCUDA(launch_fill_random_col(st, N, Vtmp, ldb, j, opts.seed, kStreamFill, fill_counter++));
+  int k_i = n_first;
+
+  // ---- Step 3
+  int k_c = 0, k_sub = 0, k_act = 0;
+  std::vector<double> eval_locked;
+  int64_t rep_counter = 0;
+  int n_rep_total = 0, n_spmm = 0, it = 0;
+  bool converged = false;
+  std::vector<double> Dh(act_max);
+  // mixed path: per filter-input column, the tested column of Step 12 whose residual it
+  // filters (-1: plain column) and its Ritz value
+  std::vector<int> mix_src(b, -1);
+  std::vector<double> mix_theta(b, NAN);
+  if (prec == BCHDAV_PREC_MIXED) BCHDAV_TRY(h->ensure(h->Rres, (size_t)N * ldb * sizeof(double)));
+
+  while (it < itmax) {
+    ++it;
+    // Step 5: Chebyshev filter
+    tm_filter.start(st);
+    if (prec == BCHDAV_PREC_MIXED) {
+      BCHDAV_TRY(run_filter_mixed(h, A, val32, Vtmp, ldb, h->Rres.as<double>(), ldb, mix_src.data(),
+                                  mix_theta.data(), b, m, low_nwb, upperb, lowb, Xo, ldb,
+                                  &filter_bytes));
+    } else {
+      BCHDAV_TRY(run_filter(h, A, val32, Vtmp, ldb, b, m, low_nwb, upperb, lowb, prec, Xo, ldb,
+                            &filter_bytes));
+    }
+    tm_filter.stop(st);
+    n_spmm += m;
+    // Step 6: orthonormalise against V(:, 1:k_sub)
+    tm_orth.start(st);
+    int nrep = 0;
+    const int k_orth = k_sub;
+    BCHDAV_TRY(run_orth(h, N, V, ldv, k_sub, Xo, ldb, b, opts.seed, tau_dep, &rep_counter, &nrep));
+    n_rep_total += nrep;
+    HCUDA(launch_copy_block(st, N, b, Xo, ldb, V + k_sub, ldv));
+    tm_orth.stop(st);
+    // Step 7: W(:, k_act+1 : k_act+b) = A V_new
+    tm_spmm.start(st);
+    HCUDA(launch_spmm_axpby<double>(st, N, A->rowptr, A->colidx, A->val, Xo, ldb, b, W + k_act, ldw,
+                                    nullptr, 0, 1.0, 0.0, 0.0));
+    tm_spmm.stop(st);
+    ++n_spmm;
+    k_act += b;
+    k_sub += b;
+    // Step 8: H(1:k_act, new) = V(:, k_c+1:k_sub)^T W_new, symmetrise
+    tm_h.start(st);
+    HCUDA(launch_gemm_tn_partial(st, N, V + k_c, ldv, k_act, W + (k_act - b), ldw, b,
+                                 h->part.as<double>(), chunks));
+    HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k_act * b, h->G.as<double>(), 1.0));
+    HCUDA(launch_h_update(st, Hm, act_max, h->G.as<double>(), k_act, b));
+    tm_h.stop(st);
+    // Step 9: H Y = Y D (ascending)
+    tm_eig.start(st);
+    HCUDA(launch_eigh(st, k_act, Hm, act_max, Dd, Ym, act_max, h->eigw.as<double>(), eig_status));
+    tm_eig.stop(st);
+    HCUDA(cudaMemcpyAsync(hp, Dd, k_act * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HCUDA(cudaMemcpyAsync(hp + act_max, eig_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    const int k_old = k_act;
+    // Step 10: inner restart
+    if (k_act + b > act_max) {
+      k_act = k_ri;
+      k_sub = k_act + k_c;
+    }
+    // Step 11: rotation V(:, k_c+1 : k_c+k_act) = V(:, k_c+1 : k_c+k_old) Y(:, 1:k_act); W likewise
+    tm_rot.start(st);
+    HCUDA(launch_gemm_nn_inplace(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act));
+    HCUDA(launch_gemm_nn_inplace(st, N, W, ldw, k_old, Ym, act_max, k_act));
+    tm_rot.stop(st);
+    // Step 12: residuals of the leading k_b Ritz pairs
+    const int nt = std::min(b, k_act);
+    tm_res.start(st);
+    int nparts = 0;
+    HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c, ldv, nt, Dd,
+                            h->part.as<double>(), &nparts,
+                            prec == BCHDAV_PREC_MIXED ? h->Rres.as<double>() : nullptr, ldb));
+    HCUDA(launch_reduce_partials(st, h->part.as<double>(), nparts, 2 * nt, dsel, 1.0));
+    HCUDA(cudaMemcpyAsync(hp + act_max + 1, dsel, 2 * nt * sizeof(double), cudaMemcpyDeviceToHost, st));
+    tm_res.stop(st);
+    ++n_spmm;
+    HCUDA(cudaStreamSynchronize(st));
+    collect();
+    if (reinterpret_cast<int*>(hp + act_max)[0] != 0) {
+      h->set_error(BCHDAV_ERR_NONFINITE, "Rayleigh-Ritz eigensolver did not converge");
+      return BCHDAV_ERR_NONFINITE;
+    }
+    for (int i = 0; i < k_old; ++i) Dh[i] = hp[i];
+    std::vector<double> rel(nt);
+    bool finite = true;
+    for (int j = 0; j < nt; ++j) {
+      double r2 = hp[act_max + 1 + j], v2 = hp[act_max + 1 + nt + j];
+      rel[j] = std::sqrt(r2) / std::sqrt(v2);
+      if (!std::isfinite(rel[j])) finite = false;
+    }
+    for (int i = 0; i < k_old; ++i)
+      if (!std::isfinite(Dh[i])) finite = false;
+    if (!finite) {
+      h->set_error(BCHDAV_ERR_NONFINITE, "non-finite Ritz value or residual");
+      return BCHDAV_ERR_NONFINITE;
+    }
+    // convergence + stable partition (converged first)
+    std::vector<int> order;
+    order.reserve(nt);
+    for (int j = 0; j < nt; ++j)
+      if (rel[j] <= tol) order.push_back(j);
+    const int e_c = (int)order.size();
+    for (int j = 0; j < nt; ++j)
+      if (!(rel[j] <= tol)) order.push_back(j);
+    bool identity = true;
+    for (int j = 0; j < nt; ++j) identity = identity && (order[j] == j);
+    if (!identity) {
+      int* pi = reinterpret_cast<int*>(hp + 2 * act_max + 2 * ncols + 8);
+      for (int j = 0; j < nt; ++j) pi[j] = order[j];
+      HCUDA(cudaMemcpyAsync(perm_d, pi, nt * sizeof(int), cudaMemcpyHostToDevice, st));
+      double* tmp = h->R.as<double>();
+      HCUDA(launch_gather_cols(st, N, nt, V + k_c, ldv, perm_d, tmp, ldb));
+      HCUDA(launch_copy_block(st, N, nt, tmp, ldb, V + k_c, ldv));
+      HCUDA(launch_gather_cols(st, N, nt, W, ldw, perm_d, tmp, ldb));
+      HCUDA(launch_copy_block(st, N, nt, tmp, ldb, W, ldw));
+      std::vector<double> dn(nt);
+      for (int j = 0; j < nt; ++j) dn[j] = Dh[order[j]];
+      for (int j = 0; j < nt; ++j) Dh[j] = dn[j];
+    }
+    for (int j = 0; j < e_c; ++j) eval_locked.push_back(Dh[j]);
+    k_c += e_c;
+    double maxres = 0.0;
+    for (double r : rel) maxres = std::max(maxres, r);
+    if (opts.record_history) {
+      bchdav_iter_record rec;
+      std::memset(&rec, 0, sizeof(rec));
+      rec.it = it;
+      rec.k_c = k_c;
+      rec.e_c = e_c;
+      rec.k_act = k_act;
+      rec.k_sub = k_sub;
+      rec.k_old = k_old;
+      rec.n_rep = nrep;
+      rec.k_orth = k_orth;
+      rec.low_nwb = low_nwb;
+      rec.max_resid = maxres;
+      h->history.push_back(rec);
+    }
+    // Step 13: exit
+    if (k_c >= k) {
+      converged = true;
+      break;
+    }
+    // Step 14: drop the converged columns of W
+    if (e_c > 0) {
+      HCUDA(launch_shift_cols_left(st, N, W, ldw, k_act - e_c, e_c));
+      k_act -= e_c;
+    }
+    // Step 15: H = diag(non-converged Ritz values)
+    std::vector<double> d_act(Dh.begin() + e_c, Dh.begin() + e_c + k_act);
+    // Step 16: outer restart
+    if (k_sub + b > dim_max) {
+      const int k_ro = dim_max - 2 * b - k_c;
+      k_act = std::min(k_act, std::max(k_ro, b));
+      k_sub = k_c + k_act;
+    }
+    for (int i = 0; i < (int)d_act.size(); ++i) hp[i] = d_act[i];
+    HCUDA(cudaMemcpyAsync(Dd, hp, std::max<size_t>(d_act.size(), 1) * sizeof(double),
+                          cudaMemcpyHostToDevice, st));
+    HCUDA(launch_h_diag(st, Hm, act_max, Dd, k_act, act_max));
+    // Step 17: next filter input
+    const int n_i = (k_init > k_i) ? std::min(e_c, k_init - k_i) : 0;
+    const int n_r = std::min(b - n_i, k_act);
+    const int n_x = b - n_i - n_r;
+    if (n_i > 0)
+      HCUDA(launch_copy_block(st, N, n_i, opts.v_init + k_i, opts.ld_v_init, Vtmp, ldb));
+    if (n_r > 0) HCUDA(launch_copy_block(st, N, n_r, V + k_c, ldv, Vtmp + n_i, ldb));
+    for (int j = 0; j < n_x; ++j)
+      HCUDA(launch_fill_random_col(st, N, Vtmp, ldb, n_i + n_r + j, opts.seed, kStreamFill,
+                                   fill_counter++));
+    k_i += n_i;
+    for (int j = 0; j < b; ++j) {
+      mix_src[j] = -1;
+      mix_theta[j] = NAN;
+    }
+    for (int j = 0; j < n_r; ++j) {
+      const int pre = e_c + j;   // position in the tested block after the partition
+      if (pre < nt) {
+        mix_src[n_i + j] = order[pre];
+        mix_theta[n_i + j] = Dh[pre];
+      }
+    }
+    // Step 18: new cut
+    if (k_act > 0) {
+      std::vector<double> tmpd(d_act.begin(), d_act.begin() + k_act);
+      double med = median_of(tmpd);
+      if (med > lowb + kLowNwbEps && med < upperb) low_nwb = med;
+    }
+  }
+  // ---- output: locked pairs sorted ascending (stable), k of them
+  const int n_out = std::min<int>(k, (int)eval_locked.size());
+  std::vector<int> idx(eval_locked.size());
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(),
+                   [&](int x, int y) { return eval_locked[x] < eval_locked[y]; });
+  double max_rel = 0.0;
+  if (n_out > 0) {
+    int* pi = reinterpret_cast<int*>(hp + 2 * act_max + 2 * ncols + 8);
+    double* ev = hp;
+    for (int j = 0; j < n_out; ++j) {
+      pi[j] = idx[j];
+      ev[j] = eval_locked[idx[j]];
+    }
+    HCUDA(cudaMemcpyAsync(perm_d, pi, n_out * sizeof(int), cudaMemcpyHostToDevice, st));
+    HCUDA(cudaMemcpyAsync(evals, ev, n_out * sizeof(double), cudaMemcpyHostToDevice, st));
+    HCUDA(launch_gather_cols(st, N, n_out, V, ldv, perm_d, evecs, k));
+    // final check: fresh float64 residuals of the returned pairs
+    for (int c0 = 0; c0 < n_out; c0 += 64) {
+      int w = std::min(64, n_out - c0);
+      int np = 0;
+      HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, evecs + c0, k, w, evals + c0,
+                              h->part.as<double>(), &np));
+      HCUDA(launch_reduce_partials(st, h->part.as<double>(), np, 2 * w, dsel, 1.0));
+      HCUDA(cudaMemcpyAsync(hp + 1024 - 128, dsel, 2 * w * sizeof(double), cudaMemcpyDeviceToHost, st));
+      HCUDA(cudaStreamSynchronize(st));
+      for (int j = 0; j < w; ++j) {
+        double r = std::sqrt(hp[1024 - 128 + j]) / std::sqrt(hp[1024 - 128 + w + j]);
+        max_rel = std::max(max_rel, r);
+      }
+    }
+  }
+  tm_total.stop(st);
+  HCUDA(cudaStreamSynchronize(st));
+  collect();
+  tm_total.collect();
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = it;
+    info->n_converged = (int)eval_locked.size();
+    info->n_spmm = n_spmm;
+    info->n_replaced = n_rep_total;
+    info->max_rel_resid = max_rel;
+    info->ms_total = tm_total.acc;
+    info->ms_filter = tm_filter.acc;
+    info->ms_orth = tm_orth.acc;
+    info->ms_spmm_w = tm_spmm.acc;
+    info->ms_h = tm_h.acc;
+    info->ms_eig = tm_eig.acc;
+    info->ms_rot = tm_rot.acc;
+    info->ms_resid = tm_res.acc;
+    info->ms_other = tm_total.acc - (tm_filter.acc + tm_orth.acc + tm_spmm.acc + tm_h.acc +
+                                     tm_eig.acc + tm_rot.acc + tm_res.acc);
+    info->filter_bytes = filter_bytes;
+    info->filter_ms_kernels = tm_filter.acc;
+    info->n_kernel_launches =
+        (int64_t)(__atomic_load_n(&bchdav::g_launches, __ATOMIC_RELAXED) - launches0);
+  }
+  return converged ? BCHDAV_OK : BCHDAV_NOT_CONVERGED;
+}
+
+bchdav_status bchdav_solve_host(bchdav_handle h, int32_t n, int64_t nnz, const int32_t* rowptr,
+                                const int32_t* colidx, const double* val, int32_t k, int32_t b,
+                                int32_t m, int32_t act_max, double tol, const bchdav_opts* opts_in,
+                                double* evals_host, double* evecs_host, bchdav_info* info) {
+  if (!h) return BCHDAV_ERR_ARG;
+  if (n < 1 || nnz < n || nnz >= (int64_t)INT32_MAX || !rowptr || !colidx || !val || !evals_host ||
+      !evecs_host || k < 1 || k > n) {
+    h->set_error(BCHDAV_ERR_ARG, "solve_host: invalid arguments");
+    return BCHDAV_ERR_ARG;
+  }
+  bchdav_opts opts;
+  std::memset(&opts, 0, sizeof(opts));
+  if (opts_in) opts = *opts_in;
+  cudaStream_t st = h->stream;
+  BCHDAV_TRY(h->ensure(h->hrow, (size_t)(n + 1) * sizeof(int32_t)));
+  BCHDAV_TRY(h->ensure(h->hcol, (size_t)nnz * sizeof(int32_t)));
+  BCHDAV_TRY(h->ensure(h->hval, (size_t)nnz * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->hev, (size_t)k * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->hevec, (size_t)n * k * sizeof(double)));
+  HCUDA(cudaMemcpyAsync(h->hrow.p, rowptr, (size_t)(n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  HCUDA(cudaMemcpyAsync(h->hcol.p, colidx, (size_t)nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  HCUDA(cudaMemcpyAsync(h->hval.p, val, (size_t)nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (opts.k_init > 0 && opts.v_init) {
+    BCHDAV_TRY(h->ensure(h->hvinit, (size_t)n * opts.k_init * sizeof(double)));
+    HCUDA(cudaMemcpy2DAsync(h->hvinit.p, (size_t)opts.k_init * sizeof(double), opts.v_init,
+                            (size_t)opts.ld_v_init * sizeof(double),
+                            (size_t)opts.k_init * sizeof(double), (size_t)n,
+                            cudaMemcpyHostToDevice, st));
+    opts.v_init = h->hvinit.as<double>();
+    opts.ld_v_init = opts.k_init;
+  }
+  bchdav_csr A;
+  A.n = n;
+  A.nnz = nnz;
+  A.rowptr = h->hrow.as<int32_t>();
+  A.colidx = h->hcol.as<int32_t>();
+  A.val = h->hval.as<double>();
+  A.val_f32 = nullptr;
+  bchdav_status s = bchdav_solve(h, &A, k, b, m, act_max, tol, &opts, h->hev.as<double>(),
+                                 h->hevec.as<double>(), info);
+  if (s != BCHDAV_OK && s != BCHDAV_NOT_CONVERGED) return s;
+  HCUDA(cudaMemcpyAsync(evals_host, h->hev.p, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HCUDA(cudaMemcpyAsync(evecs_host, h->hevec.p, (size_t)n * k * sizeof(double),
+                        cudaMemcpyDeviceToHost, st));
+  HCUDA(cudaStreamSynchronize(st));
+  return s;
+}
+
+}  // extern "C"

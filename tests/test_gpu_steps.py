@@ -1,0 +1,203 @@
+"""Parity of each single step of the CUDA path with the oracle (through the C-ABI).
+
+Eq. (1) Laplacian assembly (bit-exact), Eq. (6) SpMM, Algorithm 3 filter
+(float64 and float32 recurrence), Step 6 orthonormalisation, Step 9 eigh.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import device_csr, oracle_csr, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import paper_2212_04443_gb300 as P
+    return P.Handle()
+
+
+GRAPHS = [
+    lambda: synth.cycle_edges(97),
+    lambda: synth.path_edges(50),
+    lambda: synth.sbm_edges(3000, 7, d_in=9, d_out=1.5, seed=5),
+    lambda: synth.sbm_edges(2500, 5, p_in=1e-3, p_out=1e-4, seed=6, reattach=False),  # isolated
+    lambda: synth.disjoint_union(synth.complete_edges(70), synth.star_edges(5000)),     # long row
+    lambda: synth.rmat_edges(12, seed=9),
+]
+
+
+@pytest.mark.parametrize("gi", range(len(GRAPHS)))
+def test_laplacian_bit_exact(H, gi):
+    g = GRAPHS[gi]()
+    # add duplicates, reversed copies and self loops: the builder must fold them
+    rng = synth.rng(100 + gi)
+    extra = rng.integers(0, g.n, 64)
+    src = np.concatenate([g.src, g.dst[:50], extra]).astype(np.int32)
+    dst = np.concatenate([g.dst, g.src[:50], extra]).astype(np.int32)
+    g2 = synth.Graph(g.n, src, dst)
+    A = device_csr(H, g2)
+    L = oracle_csr(g2)
+    assert np.array_equal(to_np(A.rowptr), L.rowptr)
+    assert np.array_equal(to_np(A.colidx), L.colidx)
+    assert np.array_equal(to_np(A.val).view(np.uint64), L.val.view(np.uint64))
+    assert np.array_equal(to_np(A.val_f32), L.val.astype(np.float32))
+    assert H.check_csr(A) == 0
+
+
+def test_laplacian_rejects_out_of_range(H):
+    import torch
+    import paper_2212_04443_gb300 as P
+    src = torch.tensor([0, 1, 5], dtype=torch.int32, device="cuda")
+    dst = torch.tensor([1, 2, 0], dtype=torch.int32, device="cuda")
+    with pytest.raises(P.BchdavError) as ei:
+        H.build_laplacian(5, src, dst)
+    assert ei.value.status == -1
+
+
+def test_check_csr_flags_unsorted(H):
+    import torch
+    import paper_2212_04443_gb300 as P
+    A = P.DeviceCSR(3, torch.tensor([0, 2, 3, 4], dtype=torch.int32, device="cuda"),
+                    torch.tensor([1, 0, 1, 2], dtype=torch.int32, device="cuda"),
+                    torch.ones(4, dtype=torch.float64, device="cuda"))
+    assert H.check_csr(A) == -2
+
+
+@pytest.mark.parametrize("b", [1, 5, 20, 33])
+def test_spmm_matches_scipy(H, b):
+    import torch
+    g = synth.sbm_edges(20011, 9, d_in=11, d_out=2, seed=3)
+    A = device_csr(H, g)
+    L = oracle_csr(g)
+    X = synth.gaussian_block(g.n, b, 1)
+    Y = to_np(H.spmm(A, torch.from_numpy(X).cuda()))
+    ref = L.scipy() @ X
+    assert np.abs(Y - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m,a,b", [(1, 0.3, 4), (11, 0.002, 5), (15, 0.55, 20), (13, 0.2, 10),
+                                   (7, 1.1, 3)])
+def test_filter_f64_matches_oracle(H, m, a, b):
+    import torch
+    g = synth.sbm_edges(30000, 12, d_in=14, d_out=2, seed=4)
+    A = device_csr(H, g)
+    L = oracle_csr(g)
+    X = synth.gaussian_block(g.n, b, 2)
+    Y = to_np(H.filter(A, torch.from_numpy(X).cuda(), m, a, 2.0, 0.0))
+    ref = oracle.chebyshev_filter(L.scipy(), X, m, a, 2.0, 0.0)
+    assert np.abs(Y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_filter_on_exact_cycle_modes(H):
+    import torch
+    n, m, a = 1000, 15, 0.35
+    g = synth.cycle_edges(n)
+    A = device_csr(H, g)
+    i = np.arange(n)
+    js = [0, 1, 7, 40, 250, 500]
+    V = np.stack([np.cos(2 * math.pi * j * i / n) for j in js], 1)
+    lam = np.array([1 - math.cos(2 * math.pi * j / n) for j in js])
+    Y = to_np(H.filter(A, torch.from_numpy(V).cuda(), m, a, 2.0, 0.0))
+    p = oracle.filter_polynomial(lam, m, a, 2.0, 0.0)
+    assert np.abs(Y - V * p).max() <= 1e-12 * max(1.0, np.abs(p).max())
+
+
+@pytest.mark.parametrize("m,a,b", [(11, 0.01, 8), (15, 0.5, 20), (13, 0.2, 10), (15, 0.3, 16)])
+def test_filter_f32_recurrence(H, m, a, b):
+    """float32 recurrence: error bounded by float32 rounding propagated through m steps."""
+    import torch
+    import paper_2212_04443_gb300 as P
+    g = synth.sbm_edges(40000, 10, d_in=15, d_out=2, seed=8)
+    A = device_csr(H, g)
+    L = oracle_csr(g)
+    X = synth.gaussian_block(g.n, b, 3)
+    Y = to_np(H.filter(A, torch.from_numpy(X).cuda(), m, a, 2.0, 0.0, precision=P.PREC_MIXED))
+    ref = oracle.chebyshev_filter(L.scipy(), X, m, a, 2.0, 0.0)
+    # per-step relative rounding 2^-24, amplified at most linearly in m by the bounded recurrence
+    assert np.abs(Y - ref).max() <= 4 * m * 2.0 ** -24 * np.abs(ref).max() * 8
+
+
+@pytest.mark.parametrize("n,k,b", [(5000, 0, 6), (5000, 40, 8), (20000, 300, 20), (777, 17, 33)])
+def test_orthonormalize_matches_oracle(H, n, k, b):
+    import torch
+    V = np.linalg.qr(synth.gaussian_block(n, k, 1))[0] if k else np.zeros((n, 0))
+    X = synth.gaussian_block(n, b, 2)
+    X[:, 1] += 1e-3 * X[:, 0]
+    Xd = torch.from_numpy(X.copy()).cuda()
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).cuda() if k else None
+    nrep, ctr = H.orthonormalize(Vd, Xd, seed=7)
+    Q = to_np(Xd)
+    Qo, nrep_o, ctr_o = oracle.dgks_orthonormalize(V, X, seed=7)
+    assert nrep == nrep_o == 0 and ctr == ctr_o
+    assert np.abs(Q.T @ Q - np.eye(b)).max() < 1e-13
+    if k:
+        assert np.abs(V.T @ Q).max() < 1e-13
+    assert np.abs(Q - Qo).max() < 1e-10
+
+
+def test_orthonormalize_replaces_dependent_columns_like_oracle(H):
+    import torch
+    n, k, b = 4000, 12, 6
+    V = np.linalg.qr(synth.gaussian_block(n, k, 4))[0]
+    X = synth.gaussian_block(n, b, 5)
+    X[:, 2] = X[:, 0] * 2.0
+    X[:, 4] = V[:, 3]
+    X[:, 5] = 0.0
+    Xd = torch.from_numpy(X.copy()).cuda()
+    nrep, ctr = H.orthonormalize(torch.from_numpy(V).cuda(), Xd, seed=11, rep_counter=3)
+    Qo, nrep_o, ctr_o = oracle.dgks_orthonormalize(V, X, seed=11, rep_counter=3)
+    Q = to_np(Xd)
+    assert (nrep, ctr) == (nrep_o, ctr_o) == (3, 6)
+    assert np.abs(Q.T @ Q - np.eye(b)).max() < 1e-13
+    assert np.abs(V.T @ Q).max() < 1e-13
+    assert np.abs(Q - Qo).max() < 1e-10
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 150, 300])
+def test_eigh_matches_lapack(H, n):
+    import torch
+    rng = synth.rng(n)
+    M = rng.standard_normal((n, n))
+    S = (M + M.T) / 2
+    D, Y = H.eigh(torch.from_numpy(S).cuda())
+    D, Y = to_np(D), to_np(Y)
+    ref = np.linalg.eigvalsh(S)
+    assert np.all(np.diff(D) >= 0)
+    assert np.abs(D - ref).max() < 1e-13 * max(1.0, np.abs(ref).max()) * max(1, n) ** 0.5
+    assert np.abs(Y.T @ Y - np.eye(n)).max() < 1e-13 * max(1, n)
+    assert np.abs(S @ Y - Y * D).max() < 1e-13 * max(1.0, np.abs(ref).max()) * max(1, n)
+
+
+def test_eigh_known_spectrum_with_repeats(H):
+    import torch
+    n = 90
+    Q = np.linalg.qr(synth.gaussian_block(n, n, 9))[0]
+    d = np.concatenate([np.zeros(10), np.full(30, 0.5), np.linspace(0.6, 2.0, 50)])
+    S = (Q * d) @ Q.T
+    S = (S + S.T) / 2
+    D, Y = H.eigh(torch.from_numpy(S).cuda())
+    D, Y = to_np(D), to_np(Y)
+    assert np.abs(D - np.sort(d)).max() < 1e-13
+    assert np.abs(Y.T @ Y - np.eye(n)).max() < 1e-12
+    assert np.abs(S @ Y - Y * D).max() < 1e-12
+
+
+def test_eigh_diagonal_plus_border(H):
+    """The shape Step 15 leaves for Step 9: diag(d) bordered by k_b new columns."""
+    import torch
+    n, b = 120, 20
+    rng = synth.rng(77)
+    S = np.diag(np.sort(rng.uniform(0, 2, n)))
+    B = 1e-3 * rng.standard_normal((n, b))
+    S[:, -b:] = B
+    S[-b:, :] = B.T
+    S[-b:, -b:] = (S[-b:, -b:] + S[-b:, -b:].T) / 2
+    D, Y = H.eigh(torch.from_numpy(S).cuda())
+    D, Y = to_np(D), to_np(Y)
+    assert np.abs(D - np.linalg.eigvalsh(S)).max() < 1e-14 * 10
+    assert np.abs(S @ Y - Y * D).max() < 1e-13
