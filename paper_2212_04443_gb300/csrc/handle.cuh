@@ -30,8 +30,14 @@ struct bchdav_handle_s {
   DevBuf hrow, hcol, hval, hvinit, hev, hevec;   // device copies for bchdav_solve_host
   DevBuf Rres, mix;   // mixed path: residual block of Step 12, per-column filter coefficients
   std::vector<bchdav_iter_record> history;
-  double* host_pinned = nullptr;   // small pinned staging area
+  // Pinned staging.  host_pinned belongs to the solve driver; host_aux to the
+  // step helpers (filter coefficients, orthonormalisation scalars).  Each helper
+  // synchronises the stream before it writes host_aux again, and nothing writes
+  // host_pinned while a copy from it may still be queued.
+  double* host_pinned = nullptr;
   size_t host_pinned_doubles = 0;
+  double* host_aux = nullptr;
+  size_t host_aux_doubles = 0;
 
   void set_error(bchdav_status, const std::string& m) { err = m; }
 
@@ -66,6 +72,22 @@ struct bchdav_handle_s {
     return BCHDAV_OK;
   }
 
+  bchdav_status ensure_aux(size_t doubles) {
+    if (host_aux_doubles >= doubles) return BCHDAV_OK;
+    cudaStreamSynchronize(stream);
+    if (host_aux) cudaFreeHost(host_aux);
+    host_aux = nullptr;
+    cudaError_t e = cudaMallocHost(&host_aux, doubles * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      err = "pinned host allocation failed";
+      host_aux_doubles = 0;
+      return BCHDAV_ERR_OOM;
+    }
+    host_aux_doubles = doubles;
+    return BCHDAV_OK;
+  }
+
   void release_all() {
     DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
                      &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix};
@@ -73,5 +95,8 @@ struct bchdav_handle_s {
     if (host_pinned) cudaFreeHost(host_pinned);
     host_pinned = nullptr;
     host_pinned_doubles = 0;
+    if (host_aux) cudaFreeHost(host_aux);
+    host_aux = nullptr;
+    host_aux_doubles = 0;
   }
 };

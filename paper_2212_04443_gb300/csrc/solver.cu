@@ -168,9 +168,10 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
   float* R32 = reinterpret_cast<float*>(
       h->mix.as<char>() + 64 * sizeof(int) + (size_t)(m + 1) * 64 * sizeof(float));
   // host: sigma sequence, p_k(theta_j), deltas
-  BCHDAV_TRY(h->ensure_pinned((size_t)(m + 1) * 64 + 128));
-  float* dh = reinterpret_cast<float*>(h->host_pinned);
-  int* sh = reinterpret_cast<int*>(h->host_pinned + (size_t)(m + 1) * 32 + 32);
+  BCHDAV_TRY(h->ensure_aux((size_t)(m + 1) * 64 + 128));
+  HCUDA(cudaStreamSynchronize(st));   // earlier copies from host_aux are complete
+  float* dh = reinterpret_cast<float*>(h->host_aux);
+  int* sh = reinterpret_cast<int*>(h->host_aux + (size_t)(m + 1) * 32 + 32);
   bool any_res = false;
   std::vector<double> pkm1(b, 1.0), pk(b, 0.0);
   for (int j = 0; j < b; ++j) {
@@ -237,11 +238,12 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   BCHDAV_TRY(h->ensure(h->G, (size_t)std::max(ka_max * b, 64) * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->norm0, (size_t)(3 * 64 + 16) * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->small, inblock_gs_scratch_doubles(b) * sizeof(double) + 64));
-  BCHDAV_TRY(h->ensure_pinned(256));
+  BCHDAV_TRY(h->ensure_aux(256));
+  HCUDA(cudaStreamSynchronize(st));   // earlier copies from host_aux are complete
   double* norm0_d = h->norm0.as<double>();
   double* fin_d = norm0_d + 64;
   int* dep_d = reinterpret_cast<int*>(norm0_d + 128);
-  double* hp = h->host_pinned;
+  double* hp = h->host_aux;
 
   auto col_norms = [&](double* out_host) -> bchdav_status {
     int nc = std::min(chunks, ceil_div(n, 256 / b));
@@ -480,8 +482,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
                                           (size_t)std::max(rparts, chunks) * 2 * 64) *
                                     sizeof(double)));
   BCHDAV_TRY(h->ensure(h->G, (size_t)std::max(ncols * b, 64) * sizeof(double)));
-  BCHDAV_TRY(h->ensure_pinned((size_t)std::max(std::max(4 * act_max + 4 * ncols, 1024),
-                                                (m + 1) * 64 + 256)));
+  BCHDAV_TRY(h->ensure_pinned((size_t)std::max(4 * act_max + 4 * ncols, 1024)));
+  BCHDAV_TRY(h->ensure_aux((size_t)(m + 1) * 64 + 256));
   const float* val32 = A->val_f32;
   if (prec == BCHDAV_PREC_MIXED && !val32) {
     BCHDAV_TRY(h->ensure(h->val32, (size_t)A->nnz * sizeof(float)));
@@ -724,6 +726,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       if (med > lowb + kLowNwbEps && med < upperb) low_nwb = med;
     }
   }
+  HCUDA(cudaStreamSynchronize(st));   // copies queued from host_pinned are complete
   // ---- output: locked pairs sorted ascending (stable), k of them
   const int n_out = std::min<int>(k, (int)eval_locked.size());
   std::vector<int> idx(eval_locked.size());
