@@ -466,9 +466,13 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   const double tau_dep = prec == BCHDAV_PREC_MIXED ? kTauDepMixed : kTauDepF64;
 
   // ---- workspace
-  const int ldv = round_up(ncols, 2), ldw = round_up(act_max, 2), ldb = round_up(b, 2);
+  // W = A V (Algorithm 2, Steps 7, 11, 14): only its newest k_b columns are ever read (Step 8
+  // builds the new columns of H from them; Step 12 recomputes A V itself), so the driver keeps
+  // just those columns and skips rotating and shifting the older ones, whose values no step
+  // reads.  Every output is unchanged.
+  const int ldv = round_up(ncols, 2), ldb = round_up(b, 2);
   BCHDAV_TRY(h->ensure(h->V, (size_t)N * ldv * sizeof(double)));
-  BCHDAV_TRY(h->ensure(h->W, (size_t)N * ldw * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->W, (size_t)N * ldb * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->Vtmp, (size_t)N * ldb * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->Xo, (size_t)N * ldb * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->R, (size_t)N * ldb * sizeof(double)));
@@ -572,7 +576,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     tm_orth.stop(st);
     // Step 7: W(:, k_act+1 : k_act+b) = A V_new
     tm_spmm.start(st);
-    HCUDA(launch_spmm_axpby<double>(st, N, A->rowptr, A->colidx, A->val, Xo, ldb, b, W + k_act, ldw,
+    HCUDA(launch_spmm_axpby<double>(st, N, A->rowptr, A->colidx, A->val, Xo, ldb, b, W, ldb,
                                     nullptr, 0, 1.0, 0.0, 0.0));
     tm_spmm.stop(st);
     ++n_spmm;
@@ -580,7 +584,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     k_sub += b;
     // Step 8: H(1:k_act, new) = V(:, k_c+1:k_sub)^T W_new, symmetrise
     tm_h.start(st);
-    HCUDA(launch_gemm_tn_partial(st, N, V + k_c, ldv, k_act, W + (k_act - b), ldw, b,
+    HCUDA(launch_gemm_tn_partial(st, N, V + k_c, ldv, k_act, W, ldb, b,
                                  h->part.as<double>(), chunks));
     HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k_act * b, h->G.as<double>(), 1.0));
     HCUDA(launch_h_update(st, Hm, act_max, h->G.as<double>(), k_act, b));
@@ -597,10 +601,9 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       k_act = k_ri;
       k_sub = k_act + k_c;
     }
-    // Step 11: rotation V(:, k_c+1 : k_c+k_act) = V(:, k_c+1 : k_c+k_old) Y(:, 1:k_act); W likewise
+    // Step 11: rotation V(:, k_c+1 : k_c+k_act) = V(:, k_c+1 : k_c+k_old) Y(:, 1:k_act)
     tm_rot.start(st);
     HCUDA(launch_gemm_nn_inplace(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act));
-    HCUDA(launch_gemm_nn_inplace(st, N, W, ldw, k_old, Ym, act_max, k_act));
     tm_rot.stop(st);
     // Step 12: residuals of the leading k_b Ritz pairs
     const int nt = std::min(b, k_act);
@@ -650,8 +653,6 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       double* tmp = h->R.as<double>();
       HCUDA(launch_gather_cols(st, N, nt, V + k_c, ldv, perm_d, tmp, ldb));
       HCUDA(launch_copy_block(st, N, nt, tmp, ldb, V + k_c, ldv));
-      HCUDA(launch_gather_cols(st, N, nt, W, ldw, perm_d, tmp, ldb));
-      HCUDA(launch_copy_block(st, N, nt, tmp, ldb, W, ldw));
       std::vector<double> dn(nt);
       for (int j = 0; j < nt; ++j) dn[j] = Dh[order[j]];
       for (int j = 0; j < nt; ++j) Dh[j] = dn[j];
@@ -680,11 +681,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       converged = true;
       break;
     }
-    // Step 14: drop the converged columns of W
-    if (e_c > 0) {
-      HCUDA(launch_shift_cols_left(st, N, W, ldw, k_act - e_c, e_c));
-      k_act -= e_c;
-    }
+    // Step 14: the converged columns leave the active space
+    if (e_c > 0) k_act -= e_c;
     // Step 15: H = diag(non-converged Ritz values)
     std::vector<double> d_act(Dh.begin() + e_c, Dh.begin() + e_c + k_act);
     // Step 16: outer restart
