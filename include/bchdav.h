@@ -191,6 +191,28 @@ bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V,
 bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t ld_h, double* D,
                           double* Y, int32_t ld_y);
 
+/* ---- allocation-free variant (no counterpart in the paper) --------------- */
+
+/* bchdav_eigh for callers that cannot allocate device memory when they call
+ * it (for example while another runtime owns all device memory through its
+ * own pool, or on a latency-critical path that must not pay the device-wide
+ * synchronisation of cudaMalloc/cudaFree).  It uses no handle and calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
+ * array inside the library (about 384 KiB per GPU, held until the process
+ * exits).  Same arguments and results as bchdav_eigh, plus the CUDA stream
+ * (cudaStream_t, NULL = legacy default stream) the work is ordered on; the
+ * call synchronises that stream before returning.
+ *  - n must be <= 128; larger n returns BCHDAV_ERR_ARG (message via
+ *    bchdav_last_error(NULL)).
+ *  - The first call on a device looks up the scratch array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one scratch array: calls whose work overlaps on the
+ *    GPU (different streams, different host threads) race and give wrong
+ *    results.  Serialise them. */
+bchdav_status bchdav_eigh_noalloc(int32_t n, const double* H, int32_t ld_h, double* D, double* Y,
+                                  int32_t ld_y, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "bchdav_create", "bchdav_destroy", "bchdav_set_stream", "bchdav_status_string",
     "bchdav_last_error", "bchdav_build_laplacian", "bchdav_free_csr", "bchdav_copy_csr", "bchdav_check_csr",
     "bchdav_solve", "bchdav_solve_host", "bchdav_history", "bchdav_filter", "bchdav_spmm",
-    "bchdav_orthonormalize", "bchdav_eigh",
+    "bchdav_orthonormalize", "bchdav_eigh", "bchdav_eigh_noalloc",
 ]
 
 
@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
         "bchdav_orthonormalize": (i32, [p, i32, p, i32, i32, p, i32, i32, u64, d,
                                         C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
         "bchdav_eigh": (i32, [p, i32, p, i32, p, p, i32]),
+        "bchdav_eigh_noalloc": (i32, [i32, p, i32, p, p, i32, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

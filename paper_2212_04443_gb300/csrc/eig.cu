@@ -7,6 +7,8 @@
 // tridiagonal matrix (Bowdler, Martin, Reinsch, Wilkinson 1968) with each
 // sweep's plane rotations recorded by one thread and applied to the rows of
 // (QZ)^T by all threads in parallel.  Eigenvalues are returned ascending.
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace bchdav {
@@ -236,4 +238,82 @@ cudaError_t launch_eigh(cudaStream_t st, int n, const double* H, int ldh, double
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of bchdav_eigh.
+//
+// Some callers cannot allocate device memory at the time they need this
+// eigensolver: code running while another runtime owns every byte of device
+// memory through its own pool, or a latency-critical path that must not take
+// the device-wide synchronisation cudaMalloc and cudaFree can imply.  For them
+// the scratch lives in this fixed, file-scope device array, sized for
+// n <= kNoAllocMaxN (3 * 128 * 128 doubles for the work area plus one status
+// word, about 384 KiB).  Every GPU that loads the library reserves it until the
+// process exits.  In host code `g_eigh_scratch` only names a host-side stand-in,
+// so its device address is fetched with cudaGetSymbolAddress, once per device,
+// with that device current, on the first call made on it; that first call
+// should therefore come before any stream capture.  All calls share the array
+// and it keeps the last call's contents: the status word is cleared on every
+// call, the kernel overwrites the work area before reading it, and calls whose
+// work overlaps on the GPU race with one another.
+namespace {
+constexpr int kNoAllocMaxN = 128;
+constexpr size_t kNoAllocWork = (size_t)3 * kNoAllocMaxN * kNoAllocMaxN;
+constexpr int kMaxDevices = 64;
+__device__ __align__(256) double g_eigh_scratch[kNoAllocWork + 32];
+std::mutex g_noalloc_mu;
+double* g_noalloc_base[kMaxDevices] = {};
+}  // namespace
+
+void set_global_error(const char* msg);
+
 }  // namespace bchdav
+
+extern "C" bchdav_status bchdav_eigh_noalloc(int32_t n, const double* H, int32_t ld_h, double* D,
+                                             double* Y, int32_t ld_y, void* cuda_stream) {
+  using namespace bchdav;
+  if (n < 1 || n > kNoAllocMaxN || ld_h < n || ld_y < n || !H || !D || !Y) {
+    set_global_error(n > kNoAllocMaxN
+                         ? "eigh_noalloc: n exceeds the fixed scratch (n <= 128)"
+                         : "eigh_noalloc: invalid arguments");
+    return BCHDAV_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    set_global_error("eigh_noalloc: no usable current device");
+    return BCHDAV_ERR_CUDA;
+  }
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_eigh_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        set_global_error("eigh_noalloc: cudaGetSymbolAddress failed");
+        return BCHDAV_ERR_CUDA;
+      }
+      g_noalloc_base[dev] = static_cast<double*>(p);
+    }
+    base = g_noalloc_base[dev];
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int* status = reinterpret_cast<int*>(base + kNoAllocWork);
+  int host_status = 0;
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_eigh(st, n, H, ld_h, D, Y, ld_y, base, status);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&host_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_global_error("eigh_noalloc: CUDA error");
+    return BCHDAV_ERR_CUDA;
+  }
+  if (host_status != 0) {
+    set_global_error("eigh_noalloc: QL iteration did not converge");
+    return BCHDAV_ERR_NONFINITE;
+  }
+  return BCHDAV_OK;
+}

@@ -298,6 +298,11 @@ double median_of(std::vector<double> v) {
 
 }  // namespace
 
+namespace bchdav {
+// Message returned by bchdav_last_error(NULL) for entry points without a handle.
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace bchdav
+
 // =====================================================================
 extern "C" {
 
