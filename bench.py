@@ -120,7 +120,8 @@ def dist():
 
 
 def rotation_flops(hist, n):
-    return sum(4.0 * n * h.k_old * h.k_act for h in hist)
+    # Step 11 on V only (the CUDA path does not rotate W)
+    return sum(2.0 * n * h.k_old * h.k_act for h in hist)
 
 
 def orth_flops(hist, n, b):

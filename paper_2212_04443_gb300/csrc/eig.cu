@@ -7,9 +7,13 @@
 // tridiagonal matrix (Bowdler, Martin, Reinsch, Wilkinson 1968) with each
 // sweep's plane rotations recorded by one thread and applied to the rows of
 // (QZ)^T by all threads in parallel.  Eigenvalues are returned ascending.
+#include <cooperative_groups.h>
+
 #include <mutex>
 
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace bchdav {
 
@@ -235,6 +239,224 @@ cudaError_t launch_eigh(cudaStream_t st, int n, const double* H, int ldh, double
     if (e != cudaSuccess) return e;
   }
   eigh_kernel<<<1, kEigThreads, smem, st>>>(n, H, ldh, D, Y, ldy, work, status); note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Multi-SM variant: parallel cyclic Jacobi.
+//
+// On GB300 a float64 operation has a long latency and one SM retires only 2
+// float64 FMA per clock, so the implicit QL recurrence (one long dependent
+// chain of divisions and square roots) and any O(n^3) work on a single SM are
+// slow.  The two-sided Jacobi method instead rotates n/2 disjoint index pairs
+// at once (round-robin "circle" ordering, n - 1 rounds per sweep): every CTA
+// computes the same rotations of a round from the current diagonal and pair
+// entries (Rutishauser's formulas), then the grid updates the disjoint 2x2
+// blocks of A <- J^T A J and the column pairs of V <- V J, and one grid barrier
+// ends the round.  Sweeps repeat until the off-diagonal mass is below
+// (eps * ||A||_F)^2.  Eigenvalues come out on the diagonal, sorted ascending
+// at the end with their columns of V.
+
+constexpr int kJacThreads = 256;
+constexpr int kJacMaxSweeps = 40;
+
+struct JacLayout {
+  double *A, *V, *red;
+  int* status;
+};
+
+__host__ __device__ inline JacLayout jac_layout(double* w, int n) {
+  JacLayout L;
+  const int np = n + (n & 1);
+  L.A = w;
+  L.V = L.A + (size_t)np * np;
+  L.red = L.V + (size_t)np * np;   // [2][grid] partial sums
+  L.status = reinterpret_cast<int*>(L.red + 2 * 4 * kSMs + 8);
+  return L;
+}
+
+size_t eigh_fast_work_doubles(int n) {
+  const size_t np = (size_t)(n + (n & 1));
+  return 2 * np * np + 2 * 4 * kSMs + 16;
+}
+
+// player at circle position `pos` in round r (n_pad players, player 0 fixed)
+__device__ __forceinline__ int jac_player(int pos, int r, int np) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + r) % (np - 1);
+}
+
+__global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const double* __restrict__ H,
+                                                                  int ldh, double* __restrict__ work,
+                                                                  double* __restrict__ Dout,
+                                                                  double* __restrict__ Y, int ldy) {
+  cg::grid_group grid = cg::this_grid();
+  const int np = n + (n & 1);   // an odd n gets a dummy index n that is never rotated
+  const int half = np / 2;
+  JacLayout L = jac_layout(work, n);
+  extern __shared__ double sj[];
+  double* cs = sj;            // half
+  double* sn = sj + half;     // half
+  int* pp = reinterpret_cast<int*>(sj + 2 * half);   // half
+  int* qq = pp + half;                               // half
+  __shared__ double s_red[33];
+  __shared__ int s_flag;
+  const int t = threadIdx.x;
+  const long long gtid = (long long)blockIdx.x * kJacThreads + t;
+  const long long gstride = (long long)gridDim.x * kJacThreads;
+  double* A = L.A;
+  double* V = L.V;
+  // A = H (symmetric, upper triangle read), padded row/column zero; V = I
+  for (long long idx = gtid; idx < (long long)np * np; idx += gstride) {
+    int i = (int)(idx / np), j = (int)(idx - (long long)i * np);
+    double a = 0.0;
+    if (i < n && j < n) a = (i <= j) ? H[(size_t)i * ldh + j] : H[(size_t)j * ldh + i];
+    A[idx] = a;
+    V[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  // ||A||_F^2 for the stopping threshold
+  double loc = 0.0;
+  for (long long idx = gtid; idx < (long long)np * np; idx += gstride) loc = fma(A[idx], A[idx], loc);
+  double tot = block_sum(loc, s_red);
+  if (t == 0) L.red[blockIdx.x] = tot;
+  grid.sync();
+  if (t == 0) {
+    double sacc = 0.0;
+    for (int g = 0; g < (int)gridDim.x; ++g) sacc += L.red[g];
+    s_red[32] = sacc;
+  }
+  __syncthreads();
+  const double eps = 2.220446049250313e-16;
+  const double thresh = eps * eps * s_red[32];
+  int status = 1;
+  for (int sweep = 0; sweep < kJacMaxSweeps; ++sweep) {
+    for (int r = 0; r < np - 1; ++r) {
+      // rotations of this round, computed identically by every CTA
+      for (int k = t; k < half; k += kJacThreads) {
+        int p = jac_player(k, r, np), q = jac_player(np - 1 - k, r, np);
+        if (p > q) {
+          int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        pp[k] = p;
+        qq[k] = q;
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          const double apq = A[(size_t)p * np + q];
+          if (apq != 0.0) {
+            const double app = A[(size_t)p * np + p], aqq = A[(size_t)q * np + q];
+            const double theta = (aqq - app) / (2.0 * apq);
+            const double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
+            c = 1.0 / sqrt(fma(tt, tt, 1.0));
+            s = tt * c;
+          }
+        }
+        cs[k] = c;
+        sn[k] = s;
+      }
+      __syncthreads();
+      // A <- J^T A J on the 2x2 blocks (K, L); V <- V J on the column pairs
+      const long long nblk = (long long)half * half;
+      for (long long idx = gtid; idx < nblk + (long long)np * half; idx += gstride) {
+        if (idx < nblk) {
+          const int K = (int)(idx / half), Lb = (int)(idx - (long long)K * half);
+          const int p1 = pp[K], q1 = qq[K], p2 = pp[Lb], q2 = qq[Lb];
+          const double c1 = cs[K], s1 = sn[K], c2 = cs[Lb], s2 = sn[Lb];
+          if (s1 == 0.0 && s2 == 0.0) continue;
+          double* a11 = A + (size_t)p1 * np + p2;
+          double* a12 = A + (size_t)p1 * np + q2;
+          double* a21 = A + (size_t)q1 * np + p2;
+          double* a22 = A + (size_t)q1 * np + q2;
+          const double x11 = *a11, x12 = *a12, x21 = *a21, x22 = *a22;
+          // rows: J1^T X
+          const double y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+          const double y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+          // columns: (J1^T X) J2
+          *a11 = c2 * y11 - s2 * y12;
+          *a12 = s2 * y11 + c2 * y12;
+          *a21 = c2 * y21 - s2 * y22;
+          *a22 = s2 * y21 + c2 * y22;
+          if (K == Lb) *a12 = *a21 = 0.0;   // the pair entry this rotation annihilates
+        } else {
+          const long long j = idx - nblk;
+          const int row = (int)(j / half), K = (int)(j - (long long)row * half);
+          const double c = cs[K], s = sn[K];
+          if (s == 0.0) continue;
+          double* vp = V + (size_t)row * np + pp[K];
+          double* vq = V + (size_t)row * np + qq[K];
+          const double xp = *vp, xq = *vq;
+          *vp = c * xp - s * xq;
+          *vq = s * xp + c * xq;
+        }
+      }
+      grid.sync();
+    }
+    // off-diagonal mass after the sweep
+    loc = 0.0;
+    for (long long idx = gtid; idx < (long long)np * np; idx += gstride) {
+      int i = (int)(idx / np), j = (int)(idx - (long long)i * np);
+      if (i != j) loc = fma(A[idx], A[idx], loc);
+    }
+    tot = block_sum(loc, s_red);
+    if (t == 0) L.red[((sweep + 1) & 1) * 4 * kSMs + blockIdx.x] = tot;
+    grid.sync();
+    if (t == 0) {
+      double sacc = 0.0;
+      for (int g = 0; g < (int)gridDim.x; ++g) sacc += L.red[((sweep + 1) & 1) * 4 * kSMs + g];
+      s_flag = (sacc <= thresh) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_flag) {
+      status = 0;
+      break;
+    }
+  }
+  // ascending order of the diagonal (stable ranks); every CTA writes a share of the output
+  for (int i = (int)gtid; i < n; i += (int)gstride) {
+    const double di = A[(size_t)i * np + i];
+    int rk = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = A[(size_t)j * np + j];
+      rk += (dj < di) || (dj == di && j < i);
+    }
+    Dout[rk] = di;
+    for (int row = 0; row < n; ++row) Y[(size_t)row * ldy + rk] = V[(size_t)row * np + i];
+  }
+  if (gtid == 0) *L.status = status;
+}
+
+cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
+                             int ldy, double* work, int* status) {
+  if (n <= 32) return launch_eigh(st, n, H, ldh, D, Y, ldy, work, status);
+  if (n > 1024) return cudaErrorInvalidValue;
+  const int np = n + (n & 1);
+  const size_t smem = (size_t)(np / 2) * (2 * sizeof(double) + 2 * sizeof(int));
+  static int max_blocks = -1;
+  if (max_blocks < 0) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel,
+                                                                  kJacThreads, 12 * 1024);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    max_blocks = per_sm * sms;
+  }
+  // enough threads for the largest round (blocks + vector pairs), at most one wave
+  long long work_items = (long long)(np / 2) * (np / 2) + (long long)np * (np / 2);
+  int grid = ceil_div(work_items, kJacThreads * 2);
+  if (grid > max_blocks) grid = max_blocks;
+  if (grid > 4 * kSMs) grid = 4 * kSMs;
+  if (grid < 1) grid = 1;
+  JacLayout L = jac_layout(work, n);
+  int nn = n, lh = ldh, ly = ldy;
+  double* wk = work;
+  void* args[] = {&nn, (void*)&H, &lh, &wk, &D, &Y, &ly};
+  note_launch();
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, grid, kJacThreads,
+                                              args, smem, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(status, L.status, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -83,6 +83,11 @@ size_t inblock_gs_scratch_doubles(int b);
 cudaError_t launch_eigh(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
                         int ldy, double* work, int* status);
 size_t eigh_work_doubles(int n);
+// Same result by parallel cyclic Jacobi over many SMs for n > 32 (launch_eigh below that);
+// work holds eigh_fast_work_doubles(n) doubles.
+cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
+                             int ldy, double* work, int* status);
+size_t eigh_fast_work_doubles(int n);
 
 // ---------------- Laplacian assembly (laplacian.cu) ----------------
 struct LapWork;

@@ -424,9 +424,10 @@ bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t l
     h->set_error(BCHDAV_ERR_ARG, "eigh: bad arguments");
     return BCHDAV_ERR_ARG;
   }
-  BCHDAV_TRY(h->ensure(h->eigw, eigh_work_doubles(n) * sizeof(double) + 64));
-  int* status_d = reinterpret_cast<int*>(h->eigw.as<char>() + eigh_work_doubles(n) * sizeof(double));
-  HCUDA(launch_eigh(h->stream, n, H, ld_h, D, Y, ld_y, h->eigw.as<double>(), status_d));
+  const size_t wd = std::max(eigh_work_doubles(n), eigh_fast_work_doubles(n));
+  BCHDAV_TRY(h->ensure(h->eigw, wd * sizeof(double) + 64));
+  int* status_d = reinterpret_cast<int*>(h->eigw.as<char>() + wd * sizeof(double));
+  HCUDA(launch_eigh_fast(h->stream, n, H, ld_h, D, Y, ld_y, h->eigw.as<double>(), status_d));
   int st = 0;
   HCUDA(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HCUDA(cudaStreamSynchronize(h->stream));
@@ -484,7 +485,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   BCHDAV_TRY(h->ensure(h->H, (size_t)act_max * act_max * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->Y, (size_t)act_max * act_max * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->D, (size_t)(act_max + 256 + ncols + 64) * sizeof(double)));
-  BCHDAV_TRY(h->ensure(h->eigw, eigh_work_doubles(act_max) * sizeof(double) + 64));
+  const size_t eig_wd = std::max(eigh_work_doubles(act_max), eigh_fast_work_doubles(act_max));
+  BCHDAV_TRY(h->ensure(h->eigw, eig_wd * sizeof(double) + 64));
   const int chunks = gemm_tn_chunks(N);
   const int rparts = spmm_resid_max_parts(N, b);
   BCHDAV_TRY(h->ensure(h->part, std::max((size_t)chunks * ncols * b,
@@ -508,8 +510,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   double* Dd = h->D.as<double>();            // act_max Ritz values
   double* dsel = Dd + act_max;               // device staging for small vectors (256)
   int* perm_d = reinterpret_cast<int*>(dsel + 256);   // ncols column indices
-  int* eig_status = reinterpret_cast<int*>(h->eigw.as<char>() +
-                                           eigh_work_doubles(act_max) * sizeof(double));
+  int* eig_status = reinterpret_cast<int*>(h->eigw.as<char>() + eig_wd * sizeof(double));
   double* hp = h->host_pinned;
   h->history.clear();
 
@@ -596,7 +597,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     tm_h.stop(st);
     // Step 9: H Y = Y D (ascending)
     tm_eig.start(st);
-    HCUDA(launch_eigh(st, k_act, Hm, act_max, Dd, Ym, act_max, h->eigw.as<double>(), eig_status));
+    HCUDA(launch_eigh_fast(st, k_act, Hm, act_max, Dd, Ym, act_max, h->eigw.as<double>(),
+                           eig_status));
     tm_eig.stop(st);
     HCUDA(cudaMemcpyAsync(hp, Dd, k_act * sizeof(double), cudaMemcpyDeviceToHost, st));
     HCUDA(cudaMemcpyAsync(hp + act_max, eig_status, sizeof(int), cudaMemcpyDeviceToHost, st));
