@@ -69,7 +69,8 @@ typedef struct {
   int32_t dim_max;          /* 0: min(max(act_max + 2b, k + 30), N)  (Sec. 4 defaults) */
   int32_t itmax;            /* 0: 1000 outer iterations */
   int32_t precision;        /* bchdav_precision */
-  int32_t reserved0;
+  int32_t dense_path;       /* 0: float64-accurate tensor-core products (split into bf16 slices)
+                               for Steps 6 and 11; 1: plain float64 FMA kernels */
   uint64_t seed;            /* seed of the random vectors the method draws (Philox4x32-10) */
   const double* v_init;     /* optional N x k_init initial block (Algorithm 2, V_init) */
   int32_t k_init;
@@ -183,6 +184,12 @@ bchdav_status bchdav_spmm(bchdav_handle h, const bchdav_csr* A, const double* X,
 bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V, int32_t ldv,
                                     int32_t k, double* X, int32_t ldx, int32_t b, uint64_t seed,
                                     double tau_dep, int64_t* rep_counter, int32_t* n_replaced);
+
+/* Step 11: V(:, 0:nb) = V(:, 0:k) Y in place (V: n x k, ldv; Y: k x nb, ld_y; nb <= k),
+ * the subspace rotation, with the same float64-accurate tensor-core product the
+ * solver uses (dense_path 0) or plain float64 FMAs (dense_path 1). */
+bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, int32_t k,
+                            const double* Y, int32_t ld_y, int32_t nb, int32_t dense_path);
 
 /* Step 9: H Y = Y D for the symmetric n x n float64 matrix H (ld_h; only the
  * upper triangle is read).  D: n eigenvalues ascending; Y: n x n, column j the

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "bchdav_create", "bchdav_destroy", "bchdav_set_stream", "bchdav_status_string",
     "bchdav_last_error", "bchdav_build_laplacian", "bchdav_free_csr", "bchdav_copy_csr", "bchdav_check_csr",
     "bchdav_solve", "bchdav_solve_host", "bchdav_history", "bchdav_filter", "bchdav_spmm",
-    "bchdav_orthonormalize", "bchdav_eigh", "bchdav_eigh_noalloc",
+    "bchdav_orthonormalize", "bchdav_rotate", "bchdav_eigh", "bchdav_eigh_noalloc",
 ]
 
 
@@ -49,7 +49,7 @@ class CSRStruct(C.Structure):
 
 class OptsStruct(C.Structure):
     _fields_ = [("dim_max", C.c_int32), ("itmax", C.c_int32), ("precision", C.c_int32),
-                ("reserved0", C.c_int32), ("seed", C.c_uint64), ("v_init", C.c_void_p),
+                ("dense_path", C.c_int32), ("seed", C.c_uint64), ("v_init", C.c_void_p),
                 ("k_init", C.c_int32), ("ld_v_init", C.c_int32), ("record_history", C.c_int32),
                 ("reserved1", C.c_int32)]
 
@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
         "bchdav_orthonormalize": (i32, [p, i32, p, i32, i32, p, i32, i32, u64, d,
                                         C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
         "bchdav_eigh": (i32, [p, i32, p, i32, p, p, i32]),
+        "bchdav_rotate": (i32, [p, i32, p, i32, i32, p, i32, i32, i32]),
         "bchdav_eigh_noalloc": (i32, [i32, p, i32, p, p, i32, p]),
     }
     for name, (res, args) in sig.items():
@@ -234,7 +235,8 @@ class Handle:
     # ---- Algorithm 2
     def solve(self, A: DeviceCSR, k: int, b: int, m: int, act_max: int, tol: float, *,
               v_init=None, precision: int = PREC_FP64, dim_max: int = 0, itmax: int = 0,
-              seed: int = 0, record_history: bool = False, evals=None, evecs=None):
+              seed: int = 0, record_history: bool = False, evals=None, evecs=None,
+              dense_path: int = 0):
         import torch
         dev = A.rowptr.device
         if evals is None:
@@ -246,6 +248,7 @@ class Handle:
         opts.itmax = itmax
         opts.precision = precision
         opts.seed = seed
+        opts.dense_path = dense_path
         opts.record_history = 1 if record_history else 0
         if v_init is not None:
             assert v_init.dtype == torch.float64 and v_init.is_cuda and v_init.stride(1) == 1
@@ -327,6 +330,13 @@ class Handle:
             self.h, X.shape[0], _ptr(V), (V.stride(0) if V is not None else 1), k, _ptr(X),
             X.stride(0), X.shape[1], seed, tau_dep, C.byref(rc), C.byref(nr)))
         return nr.value, rc.value
+
+    def rotate(self, V, Y, nb: int, dense_path: int = 0):
+        """In place: V[:, :nb] = V[:, :k] @ Y[:, :nb] (k = Y.shape[0])."""
+        k = Y.shape[0]
+        self._check(self.L.bchdav_rotate(self.h, V.shape[0], _ptr(V), V.stride(0), k, _ptr(Y),
+                                         Y.stride(0), nb, dense_path))
+        return V
 
     def eigh(self, H):
         import torch

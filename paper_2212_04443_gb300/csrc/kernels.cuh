@@ -69,6 +69,15 @@ cudaError_t launch_h_diag(cudaStream_t st, double* H, int ldh, const double* d, 
 // Non-finite check: flag |= any(!isfinite(x)).
 cudaError_t launch_check_finite(cudaStream_t st, int n, int w, const double* X, int ldx, int* flag);
 
+// ---------------- float64-accurate tensor-core products (ozaki.cu) ----------------
+// C = A B (subtract: C -= A B) for A N x K row-major, B K x nb, K <= 448; C may alias A
+// (A is read only through its slices).  work: ozaki_nn_work_bytes(n, K, nb) bytes.
+cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, int K,
+                            const double* B, int ldb, int nb, double* C, int ldc, bool subtract,
+                            void* work);
+size_t ozaki_nn_work_bytes(int n, int K, int nb);
+bool ozaki_nn_supported(int K);
+
 // ---------------- orthonormalisation (orth.cu) ----------------
 // Column-by-column classical Gram-Schmidt with two passes inside the block,
 // starting at column j0; stops at the first column found dependent and

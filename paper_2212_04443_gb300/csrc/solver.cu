@@ -157,7 +157,6 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
   const double tau = 2.0 / sigma1;
   const int ldb = round_up(b, 4);
   for (int i = 0; i < 4; ++i) BCHDAV_TRY(h->ensure(h->F[i], (size_t)n * ldb * sizeof(float)));
-  BCHDAV_TRY(h->ensure(h->Rres, (size_t)n * round_up(b, 2) * sizeof(double)));
   float* T[4] = {h->F[0].as<float>(), h->F[1].as<float>(), h->F[2].as<float>(),
                  h->F[3].as<float>()};
   // R32 lives in the fourth float buffer's twin: reuse mix buffer for coefficients
@@ -225,7 +224,8 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
 
 // ---------------- Step 6 ----------------
 bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, double* X, int ldx,
-                       int b, uint64_t seed, double tau_dep, int64_t* rep_counter, int* n_rep) {
+                       int b, uint64_t seed, double tau_dep, int64_t* rep_counter, int* n_rep,
+                       int dense_path = 0) {
   cudaStream_t st = h->stream;
   if (b > 64) {
     h->set_error(BCHDAV_ERR_ARG, "block size b must be <= 64");
@@ -263,7 +263,12 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
       for (int pass = 0; pass < 2; ++pass) {
         HCUDA(launch_gemm_tn_partial(st, n, V, ldv, k, X, ldx, b, h->part.as<double>(), chunks));
         HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k * b, h->G.as<double>(), 1.0));
-        HCUDA(launch_gemm_nn_sub(st, n, V, ldv, k, h->G.as<double>(), b, b, X, ldx));
+        if (dense_path == 0 && ozaki_nn_supported(k)) {
+          BCHDAV_TRY(h->ensure(h->oz, ozaki_nn_work_bytes(n, k, b)));
+          HCUDA(launch_ozaki_nn(st, n, V, ldv, k, h->G.as<double>(), b, b, X, ldx, true, h->oz.p));
+        } else {
+          HCUDA(launch_gemm_nn_sub(st, n, V, ldv, k, h->G.as<double>(), b, b, X, ldx));
+        }
       }
     }
     for (int j = 0; j < b; ++j) hp[j] = norm0[j];
@@ -417,6 +422,23 @@ bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V,
   return s;
 }
 
+bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, int32_t k,
+                            const double* Y, int32_t ld_y, int32_t nb, int32_t dense_path) {
+  if (!h) return BCHDAV_ERR_ARG;
+  if (n < 1 || k < 1 || nb < 1 || nb > k || ldv < k || ld_y < nb || !V || !Y ||
+      (dense_path != 0 && dense_path != 1)) {
+    h->set_error(BCHDAV_ERR_ARG, "rotate: bad arguments");
+    return BCHDAV_ERR_ARG;
+  }
+  if (dense_path == 0 && ozaki_nn_supported(k)) {
+    BCHDAV_TRY(h->ensure(h->oz, ozaki_nn_work_bytes(n, k, nb)));
+    HCUDA(launch_ozaki_nn(h->stream, n, V, ldv, k, Y, ld_y, nb, V, ldv, false, h->oz.p));
+  } else {
+    HCUDA(launch_gemm_nn_inplace(h->stream, n, V, ldv, k, Y, ld_y, nb));
+  }
+  return BCHDAV_OK;
+}
+
 bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t ld_h, double* D,
                           double* Y, int32_t ld_y) {
   if (!h) return BCHDAV_ERR_ARG;
@@ -454,7 +476,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   const int prec = opts.precision;
   if (k < 1 || k > N || b < 1 || b > 64 || m < 1 || act_max < 2 * b || act_max > N ||
       !(tol > 0) || !evals || !evecs || (prec != BCHDAV_PREC_FP64 && prec != BCHDAV_PREC_MIXED) ||
-      (opts.k_init > 0 && (!opts.v_init || opts.ld_v_init < opts.k_init))) {
+      (opts.k_init > 0 && (!opts.v_init || opts.ld_v_init < opts.k_init)) ||
+      (opts.dense_path != 0 && opts.dense_path != 1)) {
     h->set_error(BCHDAV_ERR_ARG, "solve: invalid k, b, m, act_max, tol or options");
     return BCHDAV_ERR_ARG;
   }
@@ -490,11 +513,14 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   const int chunks = gemm_tn_chunks(N);
   const int rparts = spmm_resid_max_parts(N, b);
   BCHDAV_TRY(h->ensure(h->part, std::max((size_t)chunks * ncols * b,
-                                          (size_t)std::max(rparts, chunks) * 2 * 64) *
+                                          (size_t)std::max(rparts, chunks) * 2 * 128) *
                                     sizeof(double)));
   BCHDAV_TRY(h->ensure(h->G, (size_t)std::max(ncols * b, 64) * sizeof(double)));
   BCHDAV_TRY(h->ensure_pinned((size_t)std::max(4 * act_max + 4 * ncols, 1024)));
   BCHDAV_TRY(h->ensure_aux((size_t)(m + 1) * 64 + 256));
+  if (opts.dense_path == 0)
+    BCHDAV_TRY(h->ensure(h->oz, std::max(ozaki_nn_work_bytes(N, std::min(ncols, 448), act_max),
+                                         ozaki_nn_work_bytes(N, std::min(ncols, 448), b))));
   const float* val32 = A->val_f32;
   if (prec == BCHDAV_PREC_MIXED && !val32) {
     BCHDAV_TRY(h->ensure(h->val32, (size_t)A->nnz * sizeof(float)));
@@ -556,14 +582,15 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   // filters (-1: plain column) and its Ritz value
   std::vector<int> mix_src(b, -1);
   std::vector<double> mix_theta(b, NAN);
-  if (prec == BCHDAV_PREC_MIXED) BCHDAV_TRY(h->ensure(h->Rres, (size_t)N * ldb * sizeof(double)));
+  const int ldr = round_up(2 * b, 2);
+  if (prec == BCHDAV_PREC_MIXED) BCHDAV_TRY(h->ensure(h->Rres, (size_t)N * ldr * sizeof(double)));
 
   while (it < itmax) {
     ++it;
     // Step 5: Chebyshev filter
     tm_filter.start(st);
     if (prec == BCHDAV_PREC_MIXED) {
-      BCHDAV_TRY(run_filter_mixed(h, A, val32, Vtmp, ldb, h->Rres.as<double>(), ldb, mix_src.data(),
+      BCHDAV_TRY(run_filter_mixed(h, A, val32, Vtmp, ldb, h->Rres.as<double>(), ldr, mix_src.data(),
                                   mix_theta.data(), b, m, low_nwb, upperb, lowb, Xo, ldb,
                                   &filter_bytes));
     } else {
@@ -576,7 +603,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     tm_orth.start(st);
     int nrep = 0;
     const int k_orth = k_sub;
-    BCHDAV_TRY(run_orth(h, N, V, ldv, k_sub, Xo, ldb, b, opts.seed, tau_dep, &rep_counter, &nrep));
+    BCHDAV_TRY(run_orth(h, N, V, ldv, k_sub, Xo, ldb, b, opts.seed, tau_dep, &rep_counter, &nrep,
+                        opts.dense_path));
     n_rep_total += nrep;
     HCUDA(launch_copy_block(st, N, b, Xo, ldb, V + k_sub, ldv));
     tm_orth.stop(st);
@@ -610,17 +638,27 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     }
     // Step 11: rotation V(:, k_c+1 : k_c+k_act) = V(:, k_c+1 : k_c+k_old) Y(:, 1:k_act)
     tm_rot.start(st);
-    HCUDA(launch_gemm_nn_inplace(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act));
+    if (opts.dense_path == 0 && ozaki_nn_supported(k_old)) {
+      HCUDA(launch_ozaki_nn(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act, V + k_c, ldv, false,
+                            h->oz.p));
+    } else {
+      HCUDA(launch_gemm_nn_inplace(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act));
+    }
     tm_rot.stop(st);
     // Step 12: residuals of the leading k_b Ritz pairs
     const int nt = std::min(b, k_act);
+    // the mixed path also keeps the residuals of the next k_b Ritz vectors: after locking they
+    // become filter inputs (Step 17) and are filtered in residual form; only the first nt
+    // decide convergence (Step 12)
+    const int nres = prec == BCHDAV_PREC_MIXED ? std::min(2 * b, k_act) : nt;
     tm_res.start(st);
     int nparts = 0;
-    HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c, ldv, nt, Dd,
+    HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c, ldv, nres, Dd,
                             h->part.as<double>(), &nparts,
-                            prec == BCHDAV_PREC_MIXED ? h->Rres.as<double>() : nullptr, ldb));
-    HCUDA(launch_reduce_partials(st, h->part.as<double>(), nparts, 2 * nt, dsel, 1.0));
-    HCUDA(cudaMemcpyAsync(hp + act_max + 1, dsel, 2 * nt * sizeof(double), cudaMemcpyDeviceToHost, st));
+                            prec == BCHDAV_PREC_MIXED ? h->Rres.as<double>() : nullptr, ldr));
+    HCUDA(launch_reduce_partials(st, h->part.as<double>(), nparts, 2 * nres, dsel, 1.0));
+    HCUDA(cudaMemcpyAsync(hp + act_max + 1, dsel, 2 * nres * sizeof(double), cudaMemcpyDeviceToHost,
+                          st));
     tm_res.stop(st);
     ++n_spmm;
     HCUDA(cudaStreamSynchronize(st));
@@ -633,7 +671,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     std::vector<double> rel(nt);
     bool finite = true;
     for (int j = 0; j < nt; ++j) {
-      double r2 = hp[act_max + 1 + j], v2 = hp[act_max + 1 + nt + j];
+      double r2 = hp[act_max + 1 + j], v2 = hp[act_max + 1 + nres + j];
       rel[j] = std::sqrt(r2) / std::sqrt(v2);
       if (!std::isfinite(rel[j])) finite = false;
     }
@@ -718,9 +756,9 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       mix_theta[j] = NAN;
     }
     for (int j = 0; j < n_r; ++j) {
-      const int pre = e_c + j;   // position in the tested block after the partition
-      if (pre < nt) {
-        mix_src[n_i + j] = order[pre];
+      const int pre = e_c + j;   // position in the active block after the partition
+      if (pre < nres) {
+        mix_src[n_i + j] = pre < nt ? order[pre] : pre;
         mix_theta[n_i + j] = Dh[pre];
       }
     }

@@ -185,3 +185,13 @@ def test_deterministic_repeat(H):
     a = gpu_solve(H, g, 6, 3, 11, 20)
     b = gpu_solve(H, g, 6, 3, 11, 20)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_dense_paths_agree(H):
+    """Tensor-core split products and plain float64 FMA kernels give the same solve."""
+    g = synth.sbm_edges(20000, 20, d_in=14, d_out=2, seed=13)
+    a = gpu_solve(H, g, 20, 10, 13, 50, dense_path=0)
+    b = gpu_solve(H, g, 20, 10, 13, 50, dense_path=1)
+    assert a[2].status == 0 and b[2].status == 0
+    assert [h.k_c for h in a[3]] == [h.k_c for h in b[3]]
+    assert np.abs(a[0] - b[0]).max() <= 1e-12

@@ -201,3 +201,26 @@ def test_eigh_diagonal_plus_border(H):
     D, Y = to_np(D), to_np(Y)
     assert np.abs(D - np.linalg.eigvalsh(S)).max() < 1e-14 * 10
     assert np.abs(S @ Y - Y * D).max() < 1e-13
+
+
+@pytest.mark.parametrize("n,k,nb", [(50000, 300, 240), (1001, 77, 45), (4000, 16, 16), (777, 448, 5)])
+@pytest.mark.parametrize("path", [0, 1])
+def test_rotate_matches_float64(H, n, k, nb, path):
+    """Step 11 product V(:, :nb) = V(:, :k) Y, tensor-core split (path 0) and float64 FMA (path 1)."""
+    import torch
+    rng = synth.rng(n + k)
+    V = rng.standard_normal((n, k)) / np.sqrt(n)
+    V[3] = 0.0                                   # a zero row
+    V[5, :] *= 1e-12                             # a tiny row (its own exponent)
+    V[7, 1] = 1e3                                # wide range inside one row
+    Y = np.linalg.qr(rng.standard_normal((k, k)))[0][:, :nb]
+    ref = V @ Y
+    Vd = torch.from_numpy(V.copy()).cuda()
+    H.rotate(Vd, torch.from_numpy(np.ascontiguousarray(Y)).cuda(), nb, dense_path=path)
+    out = to_np(Vd)
+    assert np.array_equal(out[:, nb:], V[:, nb:])          # columns beyond nb untouched
+    # error bound of the rounded 48-bit split of both operands (|x| < 2^E <= 2 max|x|):
+    # per entry <= K (2^-49 2^E_i max|Y_j| + max|V_i| 2^-49 2^F_j) + dropped levels <= K 2^-46 ...
+    bound = k * 2.0 ** -45 * np.abs(V).max(1)[:, None] * np.abs(Y).max(0)[None, :]
+    assert np.all(np.abs(out[:, :nb] - ref) <= bound + 1e-300)
+    assert np.abs(out[3, :nb]).max() == 0.0
