@@ -185,6 +185,13 @@ bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V,
                                     int32_t k, double* X, int32_t ldx, int32_t b, uint64_t seed,
                                     double tau_dep, int64_t* rep_counter, int32_t* n_replaced);
 
+/* Steps 6 and 8: out (ka x kb, row-major, ld = kb) = A^T B for the N x ka block A (lda)
+ * and the N x kb block B (ldb), by the float64-accurate tensor-core product (dense_path 0)
+ * or plain float64 FMAs (dense_path 1).  Deterministic (fixed reduction order). */
+bchdav_status bchdav_gram(bchdav_handle h, int32_t n, const double* A, int32_t lda, int32_t ka,
+                          const double* B, int32_t ldb, int32_t kb, double* out,
+                          int32_t dense_path);
+
 /* Step 11: V(:, 0:nb) = V(:, 0:k) Y in place (V: n x k, ldv; Y: k x nb, ld_y; nb <= k),
  * the subspace rotation, with the same float64-accurate tensor-core product the
  * solver uses (dense_path 0) or plain float64 FMAs (dense_path 1). */

@@ -32,7 +32,8 @@ EXPORTED_SYMBOLS = [
     "bchdav_create", "bchdav_destroy", "bchdav_set_stream", "bchdav_status_string",
     "bchdav_last_error", "bchdav_build_laplacian", "bchdav_free_csr", "bchdav_copy_csr", "bchdav_check_csr",
     "bchdav_solve", "bchdav_solve_host", "bchdav_history", "bchdav_filter", "bchdav_spmm",
-    "bchdav_orthonormalize", "bchdav_rotate", "bchdav_eigh", "bchdav_eigh_noalloc",
+    "bchdav_orthonormalize", "bchdav_gram", "bchdav_rotate", "bchdav_eigh",
+    "bchdav_eigh_noalloc",
 ]
 
 
@@ -111,6 +112,7 @@ def lib() -> C.CDLL:
                                         C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
         "bchdav_eigh": (i32, [p, i32, p, i32, p, p, i32]),
         "bchdav_rotate": (i32, [p, i32, p, i32, i32, p, i32, i32, i32]),
+        "bchdav_gram": (i32, [p, i32, p, i32, i32, p, i32, i32, p, i32]),
         "bchdav_eigh_noalloc": (i32, [i32, p, i32, p, p, i32, p]),
     }
     for name, (res, args) in sig.items():
@@ -330,6 +332,14 @@ class Handle:
             self.h, X.shape[0], _ptr(V), (V.stride(0) if V is not None else 1), k, _ptr(X),
             X.stride(0), X.shape[1], seed, tau_dep, C.byref(rc), C.byref(nr)))
         return nr.value, rc.value
+
+    def gram(self, A, B, dense_path: int = 0):
+        """A^T B for row-major CUDA float64 blocks with the same number of rows."""
+        import torch
+        out = torch.empty((A.shape[1], B.shape[1]), dtype=torch.float64, device=A.device)
+        self._check(self.L.bchdav_gram(self.h, A.shape[0], _ptr(A), A.stride(0), A.shape[1],
+                                       _ptr(B), B.stride(0), B.shape[1], _ptr(out), dense_path))
+        return out
 
     def rotate(self, V, Y, nb: int, dense_path: int = 0):
         """In place: V[:, :nb] = V[:, :k] @ Y[:, :nb] (k = Y.shape[0])."""

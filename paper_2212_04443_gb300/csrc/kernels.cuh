@@ -77,6 +77,11 @@ cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, in
                             void* work);
 size_t ozaki_nn_work_bytes(int n, int K, int nb);
 bool ozaki_nn_supported(int K);
+// out (ka x kb, row-major) = A^T B for A N x ka, B N x kb (any N: the reduction is cut
+// into pieces of 1024 rows whose float32 sums are exact, folded in float64).
+cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, int ka,
+                            const double* B, int ldb, int kb, double* out, void* work);
+size_t ozaki_tn_work_bytes(int n, int ka, int kb);
 
 // ---------------- orthonormalisation (orth.cu) ----------------
 // Column-by-column classical Gram-Schmidt with two passes inside the block,

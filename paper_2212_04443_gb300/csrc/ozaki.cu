@@ -22,6 +22,8 @@
 // Products: legacy warp-level mma.sync m16n8k16 (bf16 in, f32 accumulate).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace bchdav {
@@ -140,12 +142,19 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// C(rows, cols) = / -= A B from the slices.  CTA: 8 warps as 4 (rows) x 2 (cols), warp tile
-// 16 x 16 (one m16 tile, two n8 tiles); k steps of 16 double-buffered through shared memory.
-template <bool SUB>
-__global__ void __launch_bounds__(256) oz_gemm_kernel(int n, int nb, int Kp, const __nv_bfloat16* __restrict__ PA,
+// Slice product.  Rows of the result come from the planes PA (S x M x Kp, k contiguous),
+// columns from PB (S x Np x Kp).  CTA: 8 warps as 4 (rows) x 2 (cols), warp tile 16 x 16 (one
+// m16 tile, two n8 tiles); k steps of 16 double-buffered through shared memory.  blockIdx.z
+// takes k steps [z * k_split, (z + 1) * k_split).  The float32 level sums are folded into
+// float64 every kOzFlush k steps (1024 values of k, inside the exactness bound) and at the end.
+// MODE 0: C = result; 1: C -= result; 2: partial[z] (M x N, row-major) = result.
+constexpr int kOzFlush = 64;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) oz_gemm_kernel(int M, int Ma, int N, int Kp, int k_split,
+                                                      const __nv_bfloat16* __restrict__ PA,
                                                       const int* __restrict__ EA,
-                                                      const __nv_bfloat16* __restrict__ PB, int nbp,
+                                                      const __nv_bfloat16* __restrict__ PB, int Np,
                                                       const int* __restrict__ EB,
                                                       double* __restrict__ C, int ldc) {
   extern __shared__ __align__(16) unsigned char oz_smem[];
@@ -156,44 +165,65 @@ __global__ void __launch_bounds__(256) oz_gemm_kernel(int n, int nb, int Kp, con
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int wm = warp & 3, wn = warp >> 2;
   const int r0 = blockIdx.x * kOzBM, c0 = blockIdx.y * kOzBN;
-  const size_t planeA = (size_t)n * Kp, planeB = (size_t)nbp * Kp;
+  const size_t planeA = (size_t)Ma * Kp, planeB = (size_t)Np * Kp;
   const int g = lane >> 2, tig = lane & 3;
+  const int nk_all = Kp / kOzBK;
+  const int kt0 = blockIdx.z * k_split;
+  const int kt1 = min(nk_all, kt0 + k_split);
 
   auto load_stage = [&](int buf, int k0) {
-    // A: S planes x 64 rows x 2 chunks of 16 B ; B: S planes x 32 rows x 2 chunks
     for (int q = t; q < kOzS * kOzBM * 2; q += 256) {
       const int s = q / (kOzBM * 2), rem = q - s * kOzBM * 2, row = rem >> 1, half = rem & 1;
       const int gr = r0 + row;
       __nv_bfloat16* dst = &sA[buf][s][row * kOzRowStride + half * 8];
-      if (gr < n) cp_async16(dst, PA + s * planeA + (size_t)gr * Kp + k0 + half * 8);
+      if (gr < M) cp_async16(dst, PA + s * planeA + (size_t)gr * Kp + k0 + half * 8);
       else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
     for (int q = t; q < kOzS * kOzBN * 2; q += 256) {
       const int s = q / (kOzBN * 2), rem = q - s * kOzBN * 2, row = rem >> 1, half = rem & 1;
       const int gc = c0 + row;
       __nv_bfloat16* dst = &sB[buf][s][row * kOzRowStride + half * 8];
-      if (gc < nbp) cp_async16(dst, PB + s * planeB + (size_t)gc * Kp + k0 + half * 8);
+      if (gc < Np) cp_async16(dst, PB + s * planeB + (size_t)gc * Kp + k0 + half * 8);
       else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
     cp_async_commit();
   };
 
   float acc[kOzS][2][4];
+  double dacc[2][4];
 #pragma unroll
-  for (int L = 0; L < kOzS; ++L)
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dacc[j][e] = 0.0;
+  auto zero_acc = [&]() {
+#pragma unroll
+    for (int L = 0; L < kOzS; ++L)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[L][j][e] = 0.f;
+  };
+  auto flush = [&]() {
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[L][j][e] = 0.f;
+      for (int e = 0; e < 4; ++e) {
+        double v = dacc[j][e];
+#pragma unroll
+        for (int L = kOzS - 1; L >= 0; --L)
+          v = fma((double)acc[L][j][e], __longlong_as_double((long long)(1023 - kOzBits * (L + 2)) << 52), v);
+        dacc[j][e] = v;
+      }
+    zero_acc();
+  };
+  zero_acc();
 
-  const int nk = Kp / kOzBK;
-  load_stage(0, 0);
-  for (int kt = 0; kt < nk; ++kt) {
-    const int buf = kt & 1;
+  if (kt0 < kt1) load_stage(0, kt0 * kOzBK);
+  for (int kt = kt0; kt < kt1; ++kt) {
+    const int buf = (kt - kt0) & 1;
     cp_async_wait0();
     __syncthreads();
-    if (kt + 1 < nk) load_stage(buf ^ 1, (kt + 1) * kOzBK);
-    // B fragments of all slices for the warp's two n8 tiles
+    if (kt + 1 < kt1) load_stage(buf ^ 1, (kt + 1) * kOzBK);
     uint32_t bf[kOzS][2][2];
 #pragma unroll
     for (int s = 0; s < kOzS; ++s)
@@ -219,34 +249,49 @@ __global__ void __launch_bounds__(256) oz_gemm_kernel(int n, int nb, int Kp, con
         }
       }
     }
+    if (((kt - kt0 + 1) % kOzFlush) == 0) flush();
   }
-  // epilogue: combine the levels in float64 and scale by 2^(E_i + F_k)
+  flush();
+  // epilogue: scale by 2^(E_row + F_col)
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
 #pragma unroll
     for (int hrow = 0; hrow < 2; ++hrow) {
       const int row = r0 + wm * 16 + g + hrow * 8;
-      if (row >= n) continue;
+      if (row >= M) continue;
       const int Er = EA[row];
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
         const int col = c0 + wn * 16 + j * 8 + tig * 2 + cc;
-        if (col >= nb) continue;
-        const int base_exp = Er + EB[col];
-        double v = 0.0;
-#pragma unroll
-        for (int L = kOzS - 1; L >= 0; --L) {
-          const int ex = base_exp - kOzBits * (L + 2);
-          const double scale =
-              (ex > -1022) ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
-          v = fma((double)acc[L][j][hrow * 2 + cc], scale, v);
-        }
-        double* p = C + (size_t)row * ldc + col;
-        if (SUB) *p -= v;
-        else *p = v;
+        if (col >= N) continue;
+        const int ex = Er + EB[col];
+        const double scale = (ex > -1022 && ex < 1023)
+                                 ? __longlong_as_double((long long)(ex + 1023) << 52)
+                                 : ldexp(1.0, ex);
+        const double v = dacc[j][hrow * 2 + cc] * scale;
+        if (MODE == 0) C[(size_t)row * ldc + col] = v;
+        else if (MODE == 1) C[(size_t)row * ldc + col] -= v;
+        else C[(size_t)blockIdx.z * M * N + (size_t)row * N + col] = v;
       }
     }
   }
+}
+
+template <int MODE>
+static cudaError_t oz_launch_gemm(cudaStream_t st, dim3 grid, int M, int Ma, int N, int Kp, int k_split,
+                                  const __nv_bfloat16* PA, const int* EA, const __nv_bfloat16* PB,
+                                  int Np, const int* EB, double* C, int ldc) {
+  const size_t smem = sizeof(__nv_bfloat16) * 2 * kOzS * (kOzBM + kOzBN) * kOzRowStride;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  oz_gemm_kernel<MODE><<<grid, 256, smem, st>>>(M, Ma, N, Kp, k_split, PA, EA, PB, Np, EB, C, ldc);
+  note_launch();
+  return cudaGetLastError();
 }
 
 size_t ozaki_nn_work_bytes(int n, int K, int nb) {
@@ -273,23 +318,103 @@ cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, in
   oz_split_rows_kernel<<<16 * kSMs, 256, 0, st>>>(n, A, lda, K, Kp, EA, PA); note_launch();
   oz_split_cols_kernel<<<ceil_div((long long)nbp * 32, 256), 256, 0, st>>>(K, nb, B, ldb, Kp, nbp, EB,
                                                                             PB); note_launch();
-  dim3 grid(ceil_div(n, kOzBM), nbp / kOzBN);
-  const size_t smem = sizeof(__nv_bfloat16) * 2 * kOzS * (kOzBM + kOzBN) * kOzRowStride;
-  static bool attr_done[2] = {false, false};
-  if (!attr_done[subtract ? 1 : 0]) {
-    cudaError_t e = subtract ? cudaFuncSetAttribute(oz_gemm_kernel<true>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                             : cudaFuncSetAttribute(oz_gemm_kernel<false>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done[subtract ? 1 : 0] = true;
+  dim3 grid(ceil_div(n, kOzBM), nbp / kOzBN, 1);
+  const int ks = Kp / kOzBK;
+  if (subtract) return oz_launch_gemm<1>(st, grid, n, n, nb, Kp, ks, PA, EA, PB, nbp, EB, C, ldc);
+  return oz_launch_gemm<0>(st, grid, n, n, nb, Kp, ks, PA, EA, PB, nbp, EB, C, ldc);
+}
+
+// ---------------- Gram products A^T B (reduction over the N rows) ----------------
+// Column exponents of X (N x w): E[c] = max_r (exponent(x_rc) + 1), by atomicMax (order free).
+__global__ void oz_col_exp_kernel(int n, const double* __restrict__ X, int ldx, int w,
+                                  int* __restrict__ E) {
+  const int t = threadIdx.x;
+  for (int c0 = 0; c0 < w; c0 += 256) {
+    const int c = c0 + t;
+    int m = -100000;
+    if (c < w)
+      for (int r = blockIdx.x; r < n; r += gridDim.x) m = max(m, oz_exp_plus1(X[(size_t)r * ldx + c]));
+    if (c < w && m > -50000) atomicMax(E + c, m);
   }
-  if (subtract)
-    oz_gemm_kernel<true><<<grid, 256, smem, st>>>(n, nb, Kp, PA, EA, PB, nbp, EB, C, ldc);
-  else
-    oz_gemm_kernel<false><<<grid, 256, smem, st>>>(n, nb, Kp, PA, EA, PB, nbp, EB, C, ldc);
-  note_launch();
-  return cudaGetLastError();
+}
+
+__global__ void oz_fill_int_kernel(int* p, int n, int v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// columns without a nonzero entry get exponent 0
+__global__ void oz_clamp_exp_kernel(int* p, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (p[i] < -50000) p[i] = 0;
+}
+
+// Transposed slices of X (N x w): planes S x wp x Np, plane[s][c][r] = digit s of x_rc.
+// 32 x 32 tiles through shared memory so that reads and writes are both contiguous.
+__global__ void oz_split_cols_t_kernel(int n, const double* __restrict__ X, int ldx, int w, int Np,
+                                       int wp, const int* __restrict__ E,
+                                       __nv_bfloat16* __restrict__ P) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  const int r0 = blockIdx.x * 32, cb = blockIdx.y * 32;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, c = cb + tx;
+    tile[i][tx] = (r < n && c < w) ? X[(size_t)r * ldx + c] : 0.0;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)wp * Np;
+  for (int i = ty; i < 32; i += 8) {
+    const int c = cb + i, r = r0 + tx;
+    if (c >= wp || r >= Np) continue;
+    const double a = tile[tx][i];
+    int d[kOzS];
+    oz_digits(oz_fixed(a, c < w ? E[c] : 0), d);
+    const bool neg = a < 0.0;
+#pragma unroll
+    for (int s = 0; s < kOzS; ++s) P[s * plane + (size_t)c * Np + r] = oz_bf16(d[s], neg);
+  }
+}
+
+size_t ozaki_tn_work_bytes(int n, int ka, int kb) {
+  const size_t Np = (size_t)round_up(n, kOzBK);
+  const size_t kap = (size_t)round_up(ka, kOzBM), kbp = (size_t)round_up(kb, kOzBN);
+  const size_t splits = 4 * kSMs;
+  return kOzS * (kap + kbp) * Np * sizeof(__nv_bfloat16) + (kap + kbp) * sizeof(int) +
+         splits * (size_t)ka * kb * sizeof(double) + 4096;
+}
+
+cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, int ka,
+                            const double* B, int ldb, int kb, double* out, void* work) {
+  if (n <= 0 || ka <= 0 || kb <= 0) return cudaSuccess;
+  const int Np = round_up(n, kOzBK);
+  const int kap = round_up(ka, kOzBM), kbp = round_up(kb, kOzBN);
+  char* w = static_cast<char*>(work);
+  __nv_bfloat16* PA = reinterpret_cast<__nv_bfloat16*>(w);
+  __nv_bfloat16* PB = PA + (size_t)kOzS * kap * Np;
+  int* EA = reinterpret_cast<int*>(PB + (size_t)kOzS * kbp * Np);
+  int* EB = EA + kap;
+  double* partial = reinterpret_cast<double*>(
+      reinterpret_cast<char*>(EB + kbp) + (256 - (reinterpret_cast<uintptr_t>(EB + kbp) & 255)));
+  oz_fill_int_kernel<<<1, 256, 0, st>>>(EA, kap + kbp, -100000); note_launch();
+  const int rows_grid = std::min(n, 8 * kSMs);
+  oz_col_exp_kernel<<<rows_grid, 256, 0, st>>>(n, A, lda, ka, EA); note_launch();
+  oz_col_exp_kernel<<<rows_grid, 256, 0, st>>>(n, B, ldb, kb, EB); note_launch();
+  oz_clamp_exp_kernel<<<1, 256, 0, st>>>(EA, kap + kbp); note_launch();
+  dim3 ga(ceil_div(Np, 32), ceil_div(kap, 32));
+  oz_split_cols_t_kernel<<<ga, 256, 0, st>>>(n, A, lda, ka, Np, kap, EA, PA); note_launch();
+  dim3 gb(ceil_div(Np, 32), ceil_div(kbp, 32));
+  oz_split_cols_t_kernel<<<gb, 256, 0, st>>>(n, B, ldb, kb, Np, kbp, EB, PB); note_launch();
+  // split the reduction so that the grid covers the GPU about twice
+  const int tiles = (kap / kOzBM) * (kbp / kOzBN);
+  const int nk = Np / kOzBK;
+  int nsplit = std::max(1, std::min(4 * kSMs, (2 * kSMs + tiles - 1) / tiles));
+  int k_split = ceil_div(nk, nsplit);
+  k_split = round_up(k_split, kOzFlush) > nk ? k_split : round_up(k_split, kOzFlush);
+  nsplit = ceil_div(nk, k_split);
+  dim3 grid(kap / kOzBM, kbp / kOzBN, nsplit);
+  cudaError_t e =
+      oz_launch_gemm<2>(st, grid, ka, kap, kb, Np, k_split, PA, EA, PB, kbp, EB, partial, kb);
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(st, partial, nsplit, ka * kb, out, 1.0);
 }
 
 }  // namespace bchdav

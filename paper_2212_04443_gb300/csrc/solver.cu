@@ -261,8 +261,14 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   for (int attempt = 0; attempt < b + 16; ++attempt) {
     if (k > 0) {
       for (int pass = 0; pass < 2; ++pass) {
-        HCUDA(launch_gemm_tn_partial(st, n, V, ldv, k, X, ldx, b, h->part.as<double>(), chunks));
-        HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k * b, h->G.as<double>(), 1.0));
+        if (dense_path == 0) {
+          BCHDAV_TRY(h->ensure(h->oz, ozaki_tn_work_bytes(n, k, b)));
+          HCUDA(launch_ozaki_tn(st, n, V, ldv, k, X, ldx, b, h->G.as<double>(), h->oz.p));
+        } else {
+          HCUDA(launch_gemm_tn_partial(st, n, V, ldv, k, X, ldx, b, h->part.as<double>(), chunks));
+          HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k * b, h->G.as<double>(),
+                                       1.0));
+        }
         if (dense_path == 0 && ozaki_nn_supported(k)) {
           BCHDAV_TRY(h->ensure(h->oz, ozaki_nn_work_bytes(n, k, b)));
           HCUDA(launch_ozaki_nn(st, n, V, ldv, k, h->G.as<double>(), b, b, X, ldx, true, h->oz.p));
@@ -422,6 +428,27 @@ bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V,
   return s;
 }
 
+bchdav_status bchdav_gram(bchdav_handle h, int32_t n, const double* A, int32_t lda, int32_t ka,
+                          const double* B, int32_t ldb, int32_t kb, double* out,
+                          int32_t dense_path) {
+  if (!h) return BCHDAV_ERR_ARG;
+  if (n < 1 || ka < 1 || kb < 1 || lda < ka || ldb < kb || !A || !B || !out ||
+      (dense_path != 0 && dense_path != 1) || (size_t)ka * kb > 16 * 1024 * 1024) {
+    h->set_error(BCHDAV_ERR_ARG, "gram: bad arguments");
+    return BCHDAV_ERR_ARG;
+  }
+  if (dense_path == 0) {
+    BCHDAV_TRY(h->ensure(h->oz, ozaki_tn_work_bytes(n, ka, kb)));
+    HCUDA(launch_ozaki_tn(h->stream, n, A, lda, ka, B, ldb, kb, out, h->oz.p));
+  } else {
+    const int chunks = gemm_tn_chunks(n);
+    BCHDAV_TRY(h->ensure(h->part, (size_t)chunks * ka * kb * sizeof(double)));
+    HCUDA(launch_gemm_tn_partial(h->stream, n, A, lda, ka, B, ldb, kb, h->part.as<double>(), chunks));
+    HCUDA(launch_reduce_partials(h->stream, h->part.as<double>(), chunks, ka * kb, out, 1.0));
+  }
+  return BCHDAV_OK;
+}
+
 bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, int32_t k,
                             const double* Y, int32_t ld_y, int32_t nb, int32_t dense_path) {
   if (!h) return BCHDAV_ERR_ARG;
@@ -519,8 +546,9 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   BCHDAV_TRY(h->ensure_pinned((size_t)std::max(4 * act_max + 4 * ncols, 1024)));
   BCHDAV_TRY(h->ensure_aux((size_t)(m + 1) * 64 + 256));
   if (opts.dense_path == 0)
-    BCHDAV_TRY(h->ensure(h->oz, std::max(ozaki_nn_work_bytes(N, std::min(ncols, 448), act_max),
-                                         ozaki_nn_work_bytes(N, std::min(ncols, 448), b))));
+    BCHDAV_TRY(h->ensure(h->oz, std::max({ozaki_nn_work_bytes(N, std::min(ncols, 448), act_max),
+                                          ozaki_nn_work_bytes(N, std::min(ncols, 448), b),
+                                          ozaki_tn_work_bytes(N, ncols, b)})));
   const float* val32 = A->val_f32;
   if (prec == BCHDAV_PREC_MIXED && !val32) {
     BCHDAV_TRY(h->ensure(h->val32, (size_t)A->nnz * sizeof(float)));
@@ -618,9 +646,14 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     k_sub += b;
     // Step 8: H(1:k_act, new) = V(:, k_c+1:k_sub)^T W_new, symmetrise
     tm_h.start(st);
-    HCUDA(launch_gemm_tn_partial(st, N, V + k_c, ldv, k_act, W, ldb, b,
-                                 h->part.as<double>(), chunks));
-    HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k_act * b, h->G.as<double>(), 1.0));
+    if (opts.dense_path == 0) {
+      HCUDA(launch_ozaki_tn(st, N, V + k_c, ldv, k_act, W, ldb, b, h->G.as<double>(), h->oz.p));
+    } else {
+      HCUDA(launch_gemm_tn_partial(st, N, V + k_c, ldv, k_act, W, ldb, b, h->part.as<double>(),
+                                   chunks));
+      HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k_act * b, h->G.as<double>(),
+                                   1.0));
+    }
     HCUDA(launch_h_update(st, Hm, act_max, h->G.as<double>(), k_act, b));
     tm_h.stop(st);
     // Step 9: H Y = Y D (ascending)

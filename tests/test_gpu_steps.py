@@ -224,3 +224,19 @@ def test_rotate_matches_float64(H, n, k, nb, path):
     bound = k * 2.0 ** -45 * np.abs(V).max(1)[:, None] * np.abs(Y).max(0)[None, :]
     assert np.all(np.abs(out[:, :nb] - ref) <= bound + 1e-300)
     assert np.abs(out[3, :nb]).max() == 0.0
+
+
+@pytest.mark.parametrize("n,ka,kb", [(1000003, 300, 20), (5000, 77, 45), (3001, 1, 1), (70000, 340, 20)])
+@pytest.mark.parametrize("path", [0, 1])
+def test_gram_matches_float64(H, n, ka, kb, path):
+    """Steps 6/8 product A^T B with a reduction over n rows (pieces of 1024 rows when split)."""
+    import torch
+    rng = synth.rng(n + ka)
+    A = rng.standard_normal((n, ka)) / np.sqrt(n)
+    B = rng.standard_normal((n, kb))
+    A[:, 0] *= 1e-9                      # a column far below the others
+    ref = A.T @ B
+    out = to_np(H.gram(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), dense_path=path))
+    # rounded 48-bit split: |err_pq| <= n 2^-46 max|A_p| max|B_q| (+ float64 summation)
+    bound = n * 2.0 ** -45 * np.abs(A).max(0)[:, None] * np.abs(B).max(0)[None, :]
+    assert np.all(np.abs(out - ref) <= bound + 1e-13 * np.abs(ref).max())
