@@ -403,6 +403,57 @@ cudaError_t launch_h_diag(cudaStream_t st, double* H, int ldh, const double* d, 
   return cudaGetLastError();
 }
 
+// G (b x b, row-major) = R^T R, R upper triangular; Rinv = R^{-1}.  One thread (b <= 64).
+// flag = 1 when G is not numerically positive definite, when a pivot R_jj falls below
+// rel_min * sqrt(G_jj) (a near dependence inside the block that this Cholesky route does not
+// resolve) or below dep * norm0[j] (the dependence test of Step 6).
+__global__ void chol_inv_kernel(int b, const double* __restrict__ G, const double* __restrict__ norm0,
+                                double rel_min, double dep, double* __restrict__ Rinv,
+                                int* __restrict__ flag) {
+  __shared__ double R[64 * 64];
+  if (threadIdx.x != 0) return;
+  int bad = 0;
+  for (int j = 0; j < b && !bad; ++j) {
+    double djj = G[j * b + j];
+    for (int i = 0; i < j; ++i) djj -= R[i * 64 + j] * R[i * 64 + j];
+    if (!(djj > 0.0)) {
+      bad = 1;
+      break;
+    }
+    const double rjj = sqrt(djj);
+    if (!(rjj > rel_min * sqrt(G[j * b + j])) || (norm0 && !(rjj > dep * norm0[j]))) {
+      bad = 1;
+      break;
+    }
+    R[j * 64 + j] = rjj;
+    const double inv = 1.0 / rjj;
+    for (int k = j + 1; k < b; ++k) {
+      double v = G[j * b + k];
+      for (int i = 0; i < j; ++i) v -= R[i * 64 + j] * R[i * 64 + k];
+      R[j * 64 + k] = v * inv;
+    }
+  }
+  *flag = bad;
+  if (bad) return;
+  for (int j = 0; j < b; ++j) {
+    const double inv = 1.0 / R[j * 64 + j];
+    Rinv[j * b + j] = inv;
+    for (int i = j + 1; i < b; ++i) Rinv[i * b + j] = 0.0;
+    for (int i = j - 1; i >= 0; --i) {
+      double v = 0.0;
+      for (int k = i; k < j; ++k) v += Rinv[i * b + k] * R[k * 64 + j];
+      Rinv[i * b + j] = -v * inv;
+    }
+  }
+}
+
+cudaError_t launch_chol_inv(cudaStream_t st, int b, const double* G, const double* norm0,
+                            double rel_min, double dep, double* Rinv, int* flag) {
+  if (b < 1 || b > 64) return cudaErrorInvalidValue;
+  chol_inv_kernel<<<1, 32, 0, st>>>(b, G, norm0, rel_min, dep, Rinv, flag); note_launch();
+  return cudaGetLastError();
+}
+
 __global__ void check_finite_kernel(int n, int w, const double* __restrict__ X, int ldx,
                                     int* __restrict__ flag) {
   long long total = (long long)n * w;

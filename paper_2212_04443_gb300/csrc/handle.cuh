@@ -30,6 +30,7 @@ struct bchdav_handle_s {
   DevBuf hrow, hcol, hval, hvinit, hev, hevec;   // device copies for bchdav_solve_host
   DevBuf Rres, mix;   // mixed path: residual block of Step 12, per-column filter coefficients
   DevBuf oz;          // slices of the float64-accurate tensor-core products
+  DevBuf oz_vt, oz_vr, oz_xt, oz_bw, oz_part;   // cached planes: V by columns, V by rows, X by columns
   std::vector<bchdav_iter_record> history;
   // Pinned staging.  host_pinned belongs to the solve driver; host_aux to the
   // step helpers (filter coefficients, orthonormalisation scalars).  Each helper
@@ -91,7 +92,7 @@ struct bchdav_handle_s {
 
   void release_all() {
     DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
-                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz};
+                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part};
     for (DevBuf* b : all) b->release();
     if (host_pinned) cudaFreeHost(host_pinned);
     host_pinned = nullptr;

@@ -66,6 +66,9 @@ cudaError_t launch_fill_random_col(cudaStream_t st, int n, double* X, int ldx, i
 cudaError_t launch_h_update(cudaStream_t st, double* H, int ldh, const double* G, int k_act, int b);
 // H = diag(d[0:k]) (ldh x ldh cleared up to k).
 cudaError_t launch_h_diag(cudaStream_t st, double* H, int ldh, const double* d, int k, int clear);
+// Cholesky G = R^T R of a small Gram matrix and R^{-1} (see dense.cu for the flag rules).
+cudaError_t launch_chol_inv(cudaStream_t st, int b, const double* G, const double* norm0,
+                            double rel_min, double dep, double* Rinv, int* flag);
 // Non-finite check: flag |= any(!isfinite(x)).
 cudaError_t launch_check_finite(cudaStream_t st, int n, int w, const double* X, int ldx, int* flag);
 
@@ -82,6 +85,22 @@ bool ozaki_nn_supported(int K);
 cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, int ka,
                             const double* B, int ldb, int kb, double* out, void* work);
 size_t ozaki_tn_work_bytes(int n, int ka, int kb);
+// Building blocks with caller-kept slices ("planes": 8 bf16 digit planes plus exponents).
+size_t oz_planes_bytes(size_t rows, size_t kp);
+int oz_pad_k(int k);      // k padded to the k step (16)
+int oz_pad_rows(int m);   // rows padded to the row tile (64)
+int oz_pad_cols(int n);   // columns padded to the column tile (32)
+cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
+                          void* planes, int* E);
+cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, int w, int Np, int cap,
+                            int c_off, void* planes, int* E);
+cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const int* EA, int capA,
+                                int a0, int ka, const void* PB, const int* EB, int capB, int kb,
+                                double* out, double* partial);
+cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void* PA, const int* EA,
+                              const double* B, int ldb, int nb, double* C, int ldc, bool subtract,
+                              void* bwork);
+size_t oz_bwork_bytes(int K, int nb);
 
 // ---------------- orthonormalisation (orth.cu) ----------------
 // Column-by-column classical Gram-Schmidt with two passes inside the block,

@@ -15,8 +15,8 @@
 // where the terms with s + t > 9 (below 2^-54 relative) are dropped.  Each
 // alpha^s beta^t is a bf16 x bf16 -> f32 tensor-core product of integers; a
 // level sums at most 8 such products of K terms, each bounded by 64 * 64 when
-// it holds a leading digit and 32 * 32 otherwise, so for K <= 448 the float32
-// accumulation is exact (448 * (4096 + 2 * 2048 + 6 * 1024) < 2^24).  The
+// it holds a leading digit and 32 * 32 otherwise, so for K <= 1170 the float32
+// accumulation is exact (1170 * (4096 + 2 * 2048 + 6 * 1024) < 2^24).  The
 // eight level sums are combined in float64 in the epilogue.
 //
 // Products: legacy warp-level mma.sync m16n8k16 (bf16 in, f32 accumulate).
@@ -30,7 +30,7 @@ namespace bchdav {
 
 constexpr int kOzS = 8;          // slices
 constexpr int kOzBits = 6;       // bits per slice
-constexpr int kOzMaxK = 448;     // exactness bound of the per-level float32 sums
+constexpr int kOzMaxK = 448;     // bound used for the one-shot products (exact up to 1092)
 constexpr int kOzBM = 64;        // CTA tile rows
 constexpr int kOzBN = 32;        // CTA tile columns
 constexpr int kOzBK = 16;        // k step
@@ -141,6 +141,8 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // Slice product.  Rows of the result come from the planes PA (S x M x Kp, k contiguous),
 // columns from PB (S x Np x Kp).  CTA: 8 warps as 4 (rows) x 2 (cols), warp tile 16 x 16 (one
@@ -151,14 +153,15 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 constexpr int kOzFlush = 64;
 
 template <int MODE>
-__global__ void __launch_bounds__(256) oz_gemm_kernel(int M, int Ma, int N, int Kp, int k_split,
+__global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, int Kp, int k_split,
                                                       const __nv_bfloat16* __restrict__ PA,
                                                       const int* __restrict__ EA,
                                                       const __nv_bfloat16* __restrict__ PB, int Np,
                                                       const int* __restrict__ EB,
                                                       double* __restrict__ C, int ldc) {
   extern __shared__ __align__(16) unsigned char oz_smem[];
-  // sA[buf][s][row * kOzRowStride + k], sB likewise (73.7 KB: dynamic shared memory)
+  // sA[buf][s][row * kOzRowStride + k], sB likewise, then 8 float64 per thread (90 KB of
+  // dynamic shared memory: two CTAs per SM)
   auto sA = reinterpret_cast<__nv_bfloat16(*)[kOzS][kOzBM * kOzRowStride]>(oz_smem);
   auto sB = reinterpret_cast<__nv_bfloat16(*)[kOzS][kOzBN * kOzRowStride]>(
       oz_smem + sizeof(__nv_bfloat16) * 2 * kOzS * kOzBM * kOzRowStride);
@@ -190,11 +193,11 @@ __global__ void __launch_bounds__(256) oz_gemm_kernel(int M, int Ma, int N, int 
   };
 
   float acc[kOzS][2][4];
-  double dacc[2][4];
+  // float64 partial sums live in shared memory (touched only at flushes), 8 per thread
+  double* dacc = reinterpret_cast<double*>(
+      oz_smem + sizeof(__nv_bfloat16) * 2 * kOzS * (kOzBM + kOzBN) * kOzRowStride) + t * 8;
 #pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) dacc[j][e] = 0.0;
+  for (int e = 0; e < 8; ++e) dacc[e] = 0.0;
   auto zero_acc = [&]() {
 #pragma unroll
     for (int L = 0; L < kOzS; ++L)
@@ -208,11 +211,11 @@ __global__ void __launch_bounds__(256) oz_gemm_kernel(int M, int Ma, int N, int 
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        double v = dacc[j][e];
+        double v = dacc[j * 4 + e];
 #pragma unroll
         for (int L = kOzS - 1; L >= 0; --L)
           v = fma((double)acc[L][j][e], __longlong_as_double((long long)(1023 - kOzBits * (L + 2)) << 52), v);
-        dacc[j][e] = v;
+        dacc[j * 4 + e] = v;
       }
     zero_acc();
   };
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(256) oz_gemm_kernel(int M, int Ma, int N, int 
         const double scale = (ex > -1022 && ex < 1023)
                                  ? __longlong_as_double((long long)(ex + 1023) << 52)
                                  : ldexp(1.0, ex);
-        const double v = dacc[j][hrow * 2 + cc] * scale;
+        const double v = dacc[j * 4 + hrow * 2 + cc] * scale;
         if (MODE == 0) C[(size_t)row * ldc + col] = v;
         else if (MODE == 1) C[(size_t)row * ldc + col] -= v;
         else C[(size_t)blockIdx.z * M * N + (size_t)row * N + col] = v;
@@ -281,7 +284,8 @@ template <int MODE>
 static cudaError_t oz_launch_gemm(cudaStream_t st, dim3 grid, int M, int Ma, int N, int Kp, int k_split,
                                   const __nv_bfloat16* PA, const int* EA, const __nv_bfloat16* PB,
                                   int Np, const int* EB, double* C, int ldc) {
-  const size_t smem = sizeof(__nv_bfloat16) * 2 * kOzS * (kOzBM + kOzBN) * kOzRowStride;
+  const size_t smem = sizeof(__nv_bfloat16) * 2 * kOzS * (kOzBM + kOzBN) * kOzRowStride +
+                      256 * 8 * sizeof(double);
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<MODE>,
@@ -415,6 +419,117 @@ cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, in
       oz_launch_gemm<2>(st, grid, ka, kap, kb, Np, k_split, PA, EA, PB, kbp, EB, partial, kb);
   if (e != cudaSuccess) return e;
   return launch_reduce_partials(st, partial, nsplit, ka * kb, out, 1.0);
+}
+
+
+// ---------------- building blocks for cached slices ----------------
+size_t oz_planes_bytes(size_t rows, size_t kp) { return kOzS * rows * kp * sizeof(__nv_bfloat16); }
+int oz_pad_k(int k) { return round_up(k, kOzBK); }
+int oz_pad_rows(int m) { return round_up(m, kOzBM); }
+int oz_pad_cols(int n) { return round_up(n, kOzBN); }
+
+// Row slices of A (n x K) into planes S x n x Kp with exponents E[n].
+cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
+                          void* planes, int* E) {
+  __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+  oz_row_exp_kernel<<<ceil_div((long long)n * 32, 256) < 16 * kSMs ? ceil_div((long long)n * 32, 256) : 16 * kSMs,
+                      256, 0, st>>>(n, A, lda, K, E); note_launch();
+  oz_split_rows_kernel<<<16 * kSMs, 256, 0, st>>>(n, A, lda, K, Kp, E, P); note_launch();
+  return cudaGetLastError();
+}
+
+// Transposed column slices of A's w columns into rows [c0, c0 + w) of planes S x cap x Np,
+// exponents into E[c0 .. c0 + w).  Rows of the planes outside [c0, c0 + w) are untouched.
+__global__ void oz_split_cols_t_off_kernel(int n, const double* __restrict__ X, int ldx, int w, int Np,
+                                           int cap, int c_off, const int* __restrict__ E,
+                                           __nv_bfloat16* __restrict__ P) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int r0 = blockIdx.x * 32, cb = blockIdx.y * 32;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, c = cb + tx;
+    tile[i][tx] = (r < n && c < w) ? X[(size_t)r * ldx + c] : 0.0;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)cap * Np;
+  for (int i = ty; i < 32; i += 8) {
+    const int c = cb + i, r = r0 + tx;
+    if (c >= w || r >= Np) continue;
+    const double a = tile[tx][i];
+    int d[kOzS];
+    oz_digits(oz_fixed(a, E[c_off + c]), d);
+    const bool neg = a < 0.0;
+#pragma unroll
+    for (int s = 0; s < kOzS; ++s) P[s * plane + (size_t)(c_off + c) * Np + r] = oz_bf16(d[s], neg);
+  }
+}
+
+cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, int w, int Np, int cap,
+                            int c_off, void* planes, int* E) {
+  if (w <= 0) return cudaSuccess;
+  __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+  oz_fill_int_kernel<<<1, 256, 0, st>>>(E + c_off, w, -100000); note_launch();
+  oz_col_exp_kernel<<<std::min(n, 8 * kSMs), 256, 0, st>>>(n, A, lda, w, E + c_off); note_launch();
+  oz_clamp_exp_kernel<<<1, 256, 0, st>>>(E + c_off, w); note_launch();
+  dim3 g(ceil_div(Np, 32), ceil_div(w, 32));
+  oz_split_cols_t_off_kernel<<<g, 256, 0, st>>>(n, A, lda, w, Np, cap, c_off, E, P); note_launch();
+  return cudaGetLastError();
+}
+
+// zero the padding rows [from, to) of planes S x cap x Np (so a padded GEMM tile reads zeros)
+__global__ void oz_zero_rows_kernel(__nv_bfloat16* P, size_t plane, int Np, int from, int to) {
+  const long long total = (long long)(to - from) * Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total * kOzS;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i / total);
+    const long long rem = i - (long long)s * total;
+    P[s * plane + (size_t)from * Np + rem] = __float2bfloat16_rn(0.f);
+  }
+}
+
+// out (ka x kb) = A^T B from transposed planes: rows [a0, a0 + ka) of PA (S x capA x Np,
+// exponents EA) and rows [0, kb) of PB (S x capB x Np, exponents EB; capB >= round_up(kb, 32)).
+cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const int* EA, int capA,
+                                int a0, int ka, const void* PB, const int* EB, int capB, int kb,
+                                double* out, double* partial) {
+  if (ka <= 0 || kb <= 0) return cudaSuccess;
+  const __nv_bfloat16* pa = static_cast<const __nv_bfloat16*>(PA) + (size_t)a0 * Np;
+  const __nv_bfloat16* pb = static_cast<const __nv_bfloat16*>(PB);
+  const int mt = ceil_div(ka, kOzBM), nt = ceil_div(kb, kOzBN);
+  const int tiles = mt * nt;
+  const int nk = Np / kOzBK;
+  int nsplit = std::max(1, std::min(4 * kSMs, (2 * kSMs + tiles - 1) / tiles));
+  const int k_split = ceil_div(nk, nsplit);
+  nsplit = ceil_div(nk, k_split);
+  dim3 grid(mt, nt, nsplit);
+  // the planes of A are read through an offset base: their row count per plane stays capA
+  cudaError_t e = oz_launch_gemm<2>(st, grid, ka, capA, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
+                                    partial, kb);
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(st, partial, nsplit, ka * kb, out, 1.0);
+}
+
+// C (n x nb) = / -= A B from row planes of A (S x n x Kp, exponents EA) and a small B (K x nb).
+cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void* PA, const int* EA,
+                              const double* B, int ldb, int nb, double* C, int ldc, bool subtract,
+                              void* bwork) {
+  if (n <= 0 || nb <= 0 || K <= 0) return cudaSuccess;
+  if (K > kOzMaxK) return cudaErrorInvalidValue;
+  const int nbp = round_up(nb, kOzBN);
+  __nv_bfloat16* PB = static_cast<__nv_bfloat16*>(bwork);
+  int* EB = reinterpret_cast<int*>(PB + (size_t)kOzS * nbp * Kp);
+  oz_split_cols_kernel<<<ceil_div((long long)nbp * 32, 256), 256, 0, st>>>(K, nb, B, ldb, Kp, nbp, EB,
+                                                                            PB); note_launch();
+  dim3 grid(ceil_div(n, kOzBM), nbp / kOzBN, 1);
+  const __nv_bfloat16* pa = static_cast<const __nv_bfloat16*>(PA);
+  if (subtract)
+    return oz_launch_gemm<1>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
+  return oz_launch_gemm<0>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
+}
+
+size_t oz_bwork_bytes(int K, int nb) {
+  return kOzS * (size_t)round_up(nb, kOzBN) * round_up(K, kOzBK) * sizeof(__nv_bfloat16) +
+         (size_t)round_up(nb, kOzBN) * sizeof(int) + 256;
 }
 
 }  // namespace bchdav

@@ -233,9 +233,10 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   }
   const int chunks = gemm_tn_chunks(n);
   const int ka_max = std::max(k, 1);
-  const size_t part_doubles = std::max((size_t)chunks * ka_max * b, (size_t)chunks * b);
+  const size_t part_doubles = (size_t)chunks * std::max(ka_max, b) * b;
   BCHDAV_TRY(h->ensure(h->part, part_doubles * sizeof(double)));
-  BCHDAV_TRY(h->ensure(h->G, (size_t)std::max(ka_max * b, 64) * sizeof(double)));
+  const size_t g_words = (size_t)std::max(ka_max * b, 64 * 64);
+  BCHDAV_TRY(h->ensure(h->G, (g_words + 64 * 64 + 16) * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->norm0, (size_t)(3 * 64 + 16) * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->small, inblock_gs_scratch_doubles(b) * sizeof(double) + 64));
   BCHDAV_TRY(h->ensure_aux(256));
@@ -258,24 +259,72 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   std::vector<double> norm0(b);
   BCHDAV_TRY(col_norms(norm0.data()));
   *n_rep = 0;
+  // tensor-core path: slices of V (by columns for V^T X, by rows for X -= V C) are made once
+  // and serve both passes and every retry; X is sliced by columns for each Gram product
+  const bool tc = dense_path == 0 && ozaki_nn_supported(std::max(k, 1));
+  const int Np = oz_pad_k(n);
+  const int capV = oz_pad_rows(std::max(k, 1)), capX = oz_pad_cols(b);
+  const int Kp = oz_pad_k(std::max(k, 1));
+  int *Evt = nullptr, *Evr = nullptr, *Ext = nullptr;
+  if (tc) {
+    BCHDAV_TRY(h->ensure(h->oz_vt, oz_planes_bytes(capV, Np) + capV * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_vr, oz_planes_bytes(n, Kp) + (size_t)n * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_xt, oz_planes_bytes(capX, Np) + capX * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_bw, oz_bwork_bytes(std::max(k, b), std::max(b, 64))));
+    BCHDAV_TRY(h->ensure(h->oz_part, (size_t)4 * kSMs * std::max(k, b) * b * sizeof(double)));
+    BCHDAV_TRY(h->ensure(h->oz, ozaki_nn_work_bytes(n, b, b)));
+    Evt = reinterpret_cast<int*>(h->oz_vt.as<char>() + oz_planes_bytes(capV, Np));
+    Evr = reinterpret_cast<int*>(h->oz_vr.as<char>() + oz_planes_bytes(n, Kp));
+    Ext = reinterpret_cast<int*>(h->oz_xt.as<char>() + oz_planes_bytes(capX, Np));
+    if (k > 0) {
+      HCUDA(oz_slice_cols_t(st, n, V, ldv, k, Np, capV, 0, h->oz_vt.p, Evt));
+      HCUDA(oz_slice_rows(st, n, V, ldv, k, Kp, h->oz_vr.p, Evr));
+    }
+  }
+  double* Gd = h->G.as<double>();
   for (int attempt = 0; attempt < b + 16; ++attempt) {
     if (k > 0) {
       for (int pass = 0; pass < 2; ++pass) {
-        if (dense_path == 0) {
-          BCHDAV_TRY(h->ensure(h->oz, ozaki_tn_work_bytes(n, k, b)));
-          HCUDA(launch_ozaki_tn(st, n, V, ldv, k, X, ldx, b, h->G.as<double>(), h->oz.p));
+        if (tc) {
+          HCUDA(oz_slice_cols_t(st, n, X, ldx, b, Np, capX, 0, h->oz_xt.p, Ext));
+          HCUDA(oz_gram_from_planes(st, Np, h->oz_vt.p, Evt, capV, 0, k, h->oz_xt.p, Ext, capX, b,
+                                    Gd, h->oz_part.as<double>()));
+          HCUDA(oz_nn_from_planes(st, n, k, Kp, h->oz_vr.p, Evr, Gd, b, b, X, ldx, true,
+                                  h->oz_bw.p));
         } else {
           HCUDA(launch_gemm_tn_partial(st, n, V, ldv, k, X, ldx, b, h->part.as<double>(), chunks));
-          HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k * b, h->G.as<double>(),
-                                       1.0));
-        }
-        if (dense_path == 0 && ozaki_nn_supported(k)) {
-          BCHDAV_TRY(h->ensure(h->oz, ozaki_nn_work_bytes(n, k, b)));
-          HCUDA(launch_ozaki_nn(st, n, V, ldv, k, h->G.as<double>(), b, b, X, ldx, true, h->oz.p));
-        } else {
-          HCUDA(launch_gemm_nn_sub(st, n, V, ldv, k, h->G.as<double>(), b, b, X, ldx));
+          HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k * b, Gd, 1.0));
+          HCUDA(launch_gemm_nn_sub(st, n, V, ldv, k, Gd, b, b, X, ldx));
         }
       }
+    }
+    if (tc && b >= 2) {
+      // inside the block: CholQR2 (X = Q R with G = X^T X = R^T R, twice).  R_jj is the norm
+      // column j keeps after the earlier columns are projected out, i.e. the Gram-Schmidt
+      // norm, so the dependence test is the same; whenever a pivot is small (or the test
+      // fails) the exact column-by-column kernel below takes over.
+      double* Rinv = Gd + g_words;
+      int* flag = reinterpret_cast<int*>(Gd + g_words + 64 * 64);
+      for (int j = 0; j < b; ++j) hp[j] = norm0[j];
+      HCUDA(cudaMemcpyAsync(norm0_d, hp, b * sizeof(double), cudaMemcpyHostToDevice, st));
+      bool ok = true;
+      for (int pass = 0; pass < 2 && ok; ++pass) {
+        // the b x b Gram matrix and X R^{-1} are small (2 N b^2 flops): plain float64
+        HCUDA(launch_gemm_tn_partial(st, n, X, ldx, b, X, ldx, b, h->part.as<double>(), chunks));
+        HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, b * b, Gd, 1.0));
+        HCUDA(launch_chol_inv(st, b, Gd, pass == 0 ? norm0_d : nullptr, pass == 0 ? 1e-4 : 0.5,
+                              tau_dep, Rinv, flag));
+        HCUDA(cudaMemcpyAsync(hp + 64, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HCUDA(cudaStreamSynchronize(st));
+        if (reinterpret_cast<int*>(hp + 64)[0] != 0) {
+          ok = false;
+          break;
+        }
+        HCUDA(launch_gemm_nn_inplace(st, n, X, ldx, b, Rinv, b, b));
+      }
+      if (ok) return BCHDAV_OK;
+      // a failed first pass left X untouched; a failed second pass (never expected after a
+      // successful first) leaves X orthogonal enough for the exact kernel to finish
     }
     for (int j = 0; j < b; ++j) hp[j] = norm0[j];
     reinterpret_cast<int*>(hp + 64)[0] = -1;
