@@ -9,6 +9,8 @@
 // (QZ)^T by all threads in parallel.  Eigenvalues are returned ascending.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -441,9 +443,16 @@ cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, d
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     max_blocks = per_sm * sms;
   }
-  // enough threads for the largest round (blocks + vector pairs), at most one wave
+  // enough threads for the largest round (blocks + vector pairs), at most one wave; the
+  // items-per-thread target trades grid-barrier cost against per-round work (tunable with
+  // BCHDAV_JACOBI_ITEMS)
+  static int items_per_thread = -1;
+  if (items_per_thread < 0) {
+    const char* env = getenv("BCHDAV_JACOBI_ITEMS");
+    items_per_thread = env ? std::max(1, atoi(env)) : 2;
+  }
   long long work_items = (long long)(np / 2) * (np / 2) + (long long)np * (np / 2);
-  int grid = ceil_div(work_items, kJacThreads * 2);
+  int grid = ceil_div(work_items, (long long)kJacThreads * items_per_thread);
   if (grid > max_blocks) grid = max_blocks;
   if (grid > 4 * kSMs) grid = 4 * kSMs;
   if (grid < 1) grid = 1;

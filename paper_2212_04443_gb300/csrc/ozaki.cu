@@ -330,15 +330,26 @@ cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, in
 
 // ---------------- Gram products A^T B (reduction over the N rows) ----------------
 // Column exponents of X (N x w): E[c] = max_r (exponent(x_rc) + 1), by atomicMax (order free).
-__global__ void oz_col_exp_kernel(int n, const double* __restrict__ X, int ldx, int w,
-                                  int* __restrict__ E) {
-  const int t = threadIdx.x;
-  for (int c0 = 0; c0 < w; c0 += 256) {
-    const int c = c0 + t;
+// warps walk rows, lanes walk columns (coalesced); per-block maxima, then one atomicMax per
+// column and block (max is order free: deterministic)
+__global__ void __launch_bounds__(256) oz_col_exp_kernel(int n, const double* __restrict__ X, int ldx,
+                                                         int w, int* __restrict__ E) {
+  __shared__ int sm[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * 8 + warp, nw = gridDim.x * 8;
+  for (int c0 = 0; c0 < w; c0 += 32) {
+    const int c = c0 + lane;
     int m = -100000;
     if (c < w)
-      for (int r = blockIdx.x; r < n; r += gridDim.x) m = max(m, oz_exp_plus1(X[(size_t)r * ldx + c]));
-    if (c < w && m > -50000) atomicMax(E + c, m);
+      for (int r = gw; r < n; r += nw) m = max(m, oz_exp_plus1(X[(size_t)r * ldx + c]));
+    sm[warp][lane] = m;
+    __syncthreads();
+    if (warp == 0) {
+      int mm = sm[0][lane];
+      for (int q = 1; q < 8; ++q) mm = max(mm, sm[q][lane]);
+      if (c < w && mm > -50000) atomicMax(E + c, mm);
+    }
+    __syncthreads();
   }
 }
 
@@ -399,9 +410,8 @@ cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, in
   double* partial = reinterpret_cast<double*>(
       reinterpret_cast<char*>(EB + kbp) + (256 - (reinterpret_cast<uintptr_t>(EB + kbp) & 255)));
   oz_fill_int_kernel<<<1, 256, 0, st>>>(EA, kap + kbp, -100000); note_launch();
-  const int rows_grid = std::min(n, 8 * kSMs);
-  oz_col_exp_kernel<<<rows_grid, 256, 0, st>>>(n, A, lda, ka, EA); note_launch();
-  oz_col_exp_kernel<<<rows_grid, 256, 0, st>>>(n, B, ldb, kb, EB); note_launch();
+  oz_col_exp_kernel<<<std::min(ceil_div(n, 64), 4 * kSMs), 256, 0, st>>>(n, A, lda, ka, EA); note_launch();
+  oz_col_exp_kernel<<<std::min(ceil_div(n, 64), 4 * kSMs), 256, 0, st>>>(n, B, ldb, kb, EB); note_launch();
   oz_clamp_exp_kernel<<<1, 256, 0, st>>>(EA, kap + kbp); note_launch();
   dim3 ga(ceil_div(Np, 32), ceil_div(kap, 32));
   oz_split_cols_t_kernel<<<ga, 256, 0, st>>>(n, A, lda, ka, Np, kap, EA, PA); note_launch();
@@ -469,7 +479,7 @@ cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, in
   if (w <= 0) return cudaSuccess;
   __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
   oz_fill_int_kernel<<<1, 256, 0, st>>>(E + c_off, w, -100000); note_launch();
-  oz_col_exp_kernel<<<std::min(n, 8 * kSMs), 256, 0, st>>>(n, A, lda, w, E + c_off); note_launch();
+  oz_col_exp_kernel<<<std::min(ceil_div(n, 64), 4 * kSMs), 256, 0, st>>>(n, A, lda, w, E + c_off); note_launch();
   oz_clamp_exp_kernel<<<1, 256, 0, st>>>(E + c_off, w); note_launch();
   dim3 g(ceil_div(Np, 32), ceil_div(w, 32));
   oz_split_cols_t_off_kernel<<<g, 256, 0, st>>>(n, A, lda, w, Np, cap, c_off, E, P); note_launch();
