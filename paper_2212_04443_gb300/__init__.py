@@ -84,9 +84,9 @@ def lib() -> C.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    from .build import needs_build
+    from .build import build as _build, needs_build
     if needs_build():
-        build()
+        _build()
     if not os.path.exists(_LIB_PATH):
         raise RuntimeError(f"CUDA library missing: {_LIB_PATH}")
     L = C.CDLL(_LIB_PATH)

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "kernels.cuh"
 
 struct DevBuf {
   void* p = nullptr;
@@ -31,6 +32,10 @@ struct bchdav_handle_s {
   DevBuf Rres, mix;   // mixed path: residual block of Step 12, per-column filter coefficients
   DevBuf oz;          // slices of the float64-accurate tensor-core products
   DevBuf oz_vt, oz_vr, oz_xt, oz_bw, oz_part;   // cached planes: V by columns, V by rows, X by columns
+  // long-row schedule of the CSR matrix in use (rows over the segment threshold)
+  DevBuf lg_cnt, lg_off, lg_tiles, lg_row, lg_pseg;
+  bchdav::SpmmLong lg;
+  const bchdav::SpmmLong* long_rows() const { return lg.n_seg > 0 ? &lg : nullptr; }
   std::vector<bchdav_iter_record> history;
   // Pinned staging.  host_pinned belongs to the solve driver; host_aux to the
   // step helpers (filter coefficients, orthonormalisation scalars).  Each helper
@@ -92,7 +97,9 @@ struct bchdav_handle_s {
 
   void release_all() {
     DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
-                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part};
+                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part,
+                     &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg};
+    lg = bchdav::SpmmLong();
     for (DevBuf* b : all) b->release();
     if (host_pinned) cudaFreeHost(host_pinned);
     host_pinned = nullptr;

@@ -4,7 +4,30 @@
 
 namespace bchdav {
 
+// Exclusive scan of int counts (+ add_one each) into int64 offsets out[0..n] (laplacian.cu);
+// tile_sums holds ceil(n / 2048) + 1 values.
+cudaError_t exclusive_scan(cudaStream_t st, int n, const int* in, int add_one, long long* out,
+                           long long* tile_sums);
+inline int scan_tile_count(int n) { return (n + 2047) / 2048 + 1; }
+
 // ---------------- SpMM family (spmm.cu) ----------------
+// Rows with more than kLongRow nonzeros are cut into segments of kLongRow nonzeros, each
+// reduced by its own CTA into pseg (n_seg x b, in the SpMM's value type) before the row
+// kernel adds them up in segment order.
+constexpr int kLongRow = 1024;
+struct SpmmLong {
+  long long n_seg = 0;                 // 0: no long rows (the row kernel does every row)
+  const long long* seg_off = nullptr;  // n + 1: row r owns segments [seg_off[r], seg_off[r+1])
+  const int* seg_row = nullptr;        // n_seg: row of each segment
+  void* pseg = nullptr;                // n_seg * b values of workspace
+};
+// Builds seg_off / seg_row for rowptr (one host synchronisation to read the segment count).
+// cnt_work: n ints; tile_sums: scan_tile_count(n) values; seg_row capacity seg_cap.
+cudaError_t build_spmm_long(cudaStream_t st, int n, const int* rowptr, int* cnt_work,
+                            long long* seg_off, long long* tile_sums, int* seg_row,
+                            long long seg_cap, long long* host_total, long long* n_seg);
+long long spmm_long_seg_cap(long long nnz);
+
 // Y = alpha * (A X) + beta * X + gamma * Z + diag(delta) R, row by row (Eq. (6)
 // with the epilogue of Algorithm 3).  Z may be NULL (gamma ignored); R may be
 // NULL (delta, one coefficient per column on the device, ignored).
@@ -12,7 +35,8 @@ template <typename T>
 cudaError_t launch_spmm_axpby(cudaStream_t st, int n, const int* rowptr, const int* colidx,
                               const T* val, const T* X, int ldx, int b, T* Y, int ldy,
                               const T* Z, int ldz, T alpha, T beta, T gamma,
-                              const T* R = nullptr, int ldr = 0, const T* delta = nullptr);
+                              const T* R = nullptr, int ldr = 0, const T* delta = nullptr,
+                              const SpmmLong* lg = nullptr);
 
 // Residual of Step 12: for column j, r_j = (A V)_j - d_j V_j; writes per-CTA
 // partial sums of r_j^2 and v_j^2 to partial[cta * 2b + {j, b + j}] and
@@ -21,7 +45,7 @@ cudaError_t launch_spmm_axpby(cudaStream_t st, int n, const int* rowptr, const i
 cudaError_t launch_spmm_resid(cudaStream_t st, int n, const int* rowptr, const int* colidx,
                               const double* val, const double* V, int ldv, int b,
                               const double* d, double* partial, int* n_parts,
-                              double* Rout = nullptr, int ldr = 0);
+                              double* Rout = nullptr, int ldr = 0, const SpmmLong* lg = nullptr);
 int spmm_resid_max_parts(int n, int b);
 
 // ---------------- dense family (dense.cu) ----------------
@@ -86,6 +110,7 @@ cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, in
                             const double* B, int ldb, int kb, double* out, void* work);
 size_t ozaki_tn_work_bytes(int n, int ka, int kb);
 // Building blocks with caller-kept slices ("planes": 8 bf16 digit planes plus exponents).
+int oz_chunks(int Np);   // 1024-row exponent chunks of a Gram operand with Np rows
 size_t oz_planes_bytes(size_t rows, size_t kp);
 int oz_pad_k(int k);      // k padded to the k step (16)
 int oz_pad_rows(int m);   // rows padded to the row tile (64)

@@ -41,7 +41,11 @@ __global__ void count_kernel(long long ne, const int* __restrict__ src, const in
   }
 }
 
-// ---- exclusive scan of int counts into int64 offsets (three phases)
+}  // namespace
+
+// ---- exclusive scan of int counts into int64 offsets (three phases); also used by the SpMM
+// long-row schedule
+namespace bchdav {
 constexpr int kScanTile = 2048;
 
 __global__ void scan_tiles_kernel(int n, const int* __restrict__ in, int add_one,
@@ -113,6 +117,10 @@ cudaError_t exclusive_scan(cudaStream_t st, int n, const int* in, int add_one, l
       n, out, tile_sums, tile_sums + ntiles); note_launch();
   return cudaGetLastError();
 }
+
+}  // namespace bchdav
+
+namespace {
 
 __global__ void scatter_kernel(long long ne, const int* __restrict__ src, const int* __restrict__ dst,
                                const long long* __restrict__ start, int* __restrict__ fill,

@@ -19,6 +19,12 @@
 // accumulation is exact (1170 * (4096 + 2 * 2048 + 6 * 1024) < 2^24).  The
 // eight level sums are combined in float64 in the epilogue.
 //
+// Gram products A^T B reduce over the N rows, where one exponent per column would tie every
+// entry to the column's largest one (a hub vertex of a power-law graph costs the other rows
+// their low bits).  There the exponents are per column AND per chunk of kOzChunk = 1024 rows:
+// each chunk's level sums are exact in float32 by themselves and are scaled by
+// 2^{E_chunk,i + F_chunk,k} as they are folded into float64.
+//
 // Products: legacy warp-level mma.sync m16n8k16 (bf16 in, f32 accumulate).
 #include <cuda_bf16.h>
 
@@ -35,6 +41,7 @@ constexpr int kOzBM = 64;        // CTA tile rows
 constexpr int kOzBN = 32;        // CTA tile columns
 constexpr int kOzBK = 16;        // k step
 constexpr int kOzRowStride = 24; // smem row stride (bf16) of a 16-wide k tile: conflict-free
+constexpr int kOzChunk = 1024;   // rows per exponent chunk of a Gram operand (64 k steps of 16)
 
 // --- digit extraction ------------------------------------------------------
 __device__ __forceinline__ int oz_exp_plus1(double a) {
@@ -67,6 +74,11 @@ __device__ __forceinline__ void oz_digits(unsigned long long F, int (&d)[kOzS]) 
     X = (X - r) >> 6;
   }
   d[0] = (int)X;
+}
+
+__device__ __forceinline__ double oz_pow2(int ex) {
+  return (ex > -1022 && ex < 1023) ? __longlong_as_double((long long)(ex + 1023) << 52)
+                                   : ldexp(1.0, ex);
 }
 
 __device__ __forceinline__ __nv_bfloat16 oz_bf16(int d, bool neg) {
@@ -206,16 +218,24 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[L][j][e] = 0.f;
   };
-  auto flush = [&]() {
+  // MODE 2: chunk exponents, the k steps folded last lie in chunk `ch`
+  auto flush = [&](int ch) {
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        double v = dacc[j * 4 + e];
+        double v = 0.0;
 #pragma unroll
         for (int L = kOzS - 1; L >= 0; --L)
           v = fma((double)acc[L][j][e], __longlong_as_double((long long)(1023 - kOzBits * (L + 2)) << 52), v);
-        dacc[j * 4 + e] = v;
+        if (MODE == 2) {
+          const int row = r0 + wm * 16 + g + (e >> 1) * 8;
+          const int col = c0 + wn * 16 + j * 8 + tig * 2 + (e & 1);
+          v = (row < M && col < N)
+                  ? v * oz_pow2(EA[(size_t)ch * Ma + row] + EB[(size_t)ch * Np + col])
+                  : 0.0;
+        }
+        dacc[j * 4 + e] += v;
       }
     zero_acc();
   };
@@ -252,9 +272,9 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
         }
       }
     }
-    if (((kt - kt0 + 1) % kOzFlush) == 0) flush();
+    if (((kt - kt0 + 1) % kOzFlush) == 0) flush(kt / kOzFlush);
   }
-  flush();
+  flush(kt1 > kt0 ? (kt1 - 1) / kOzFlush : 0);
   // epilogue: scale by 2^(E_row + F_col)
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
@@ -262,15 +282,12 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
     for (int hrow = 0; hrow < 2; ++hrow) {
       const int row = r0 + wm * 16 + g + hrow * 8;
       if (row >= M) continue;
-      const int Er = EA[row];
+      const int Er = MODE == 2 ? 0 : EA[row];
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
         const int col = c0 + wn * 16 + j * 8 + tig * 2 + cc;
         if (col >= N) continue;
-        const int ex = Er + EB[col];
-        const double scale = (ex > -1022 && ex < 1023)
-                                 ? __longlong_as_double((long long)(ex + 1023) << 52)
-                                 : ldexp(1.0, ex);
+        const double scale = MODE == 2 ? 1.0 : oz_pow2(Er + EB[col]);
         const double v = dacc[j * 4 + hrow * 2 + cc] * scale;
         if (MODE == 0) C[(size_t)row * ldc + col] = v;
         else if (MODE == 1) C[(size_t)row * ldc + col] -= v;
@@ -329,39 +346,29 @@ cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, in
 }
 
 // ---------------- Gram products A^T B (reduction over the N rows) ----------------
-// Column exponents of X (N x w): E[c] = max_r (exponent(x_rc) + 1), by atomicMax (order free).
-// warps walk rows, lanes walk columns (coalesced); per-block maxima, then one atomicMax per
-// column and block (max is order free: deterministic)
+// Chunk column exponents of X (N x w): E[ch * cap + c_off + c] = max over rows r of chunk ch of
+// (exponent(x_rc) + 1), 0 for a chunk column without nonzeros.  Block (ch, column tile of 32):
+// warps walk the chunk's rows, lanes the columns; fixed-order max, no atomics.
 __global__ void __launch_bounds__(256) oz_col_exp_kernel(int n, const double* __restrict__ X, int ldx,
-                                                         int w, int* __restrict__ E) {
+                                                         int w, int cap, int c_off,
+                                                         int* __restrict__ E) {
   __shared__ int sm[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gw = blockIdx.x * 8 + warp, nw = gridDim.x * 8;
-  for (int c0 = 0; c0 < w; c0 += 32) {
-    const int c = c0 + lane;
-    int m = -100000;
-    if (c < w)
-      for (int r = gw; r < n; r += nw) m = max(m, oz_exp_plus1(X[(size_t)r * ldx + c]));
-    sm[warp][lane] = m;
-    __syncthreads();
-    if (warp == 0) {
-      int mm = sm[0][lane];
-      for (int q = 1; q < 8; ++q) mm = max(mm, sm[q][lane]);
-      if (c < w && mm > -50000) atomicMax(E + c, mm);
-    }
-    __syncthreads();
+  const int ch = blockIdx.x, c = blockIdx.y * 32 + lane;
+  const int r_end = min(n, (ch + 1) * kOzChunk);
+  int m = -100000;
+  if (c < w)
+    for (int r = ch * kOzChunk + warp; r < r_end; r += 8) m = max(m, oz_exp_plus1(X[(size_t)r * ldx + c]));
+  sm[warp][lane] = m;
+  __syncthreads();
+  if (warp == 0 && c < w) {
+    int mm = sm[0][lane];
+    for (int q = 1; q < 8; ++q) mm = max(mm, sm[q][lane]);
+    E[(size_t)ch * cap + c_off + c] = mm < -50000 ? 0 : mm;
   }
 }
 
-__global__ void oz_fill_int_kernel(int* p, int n, int v) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
-}
-
-// columns without a nonzero entry get exponent 0
-__global__ void oz_clamp_exp_kernel(int* p, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    if (p[i] < -50000) p[i] = 0;
-}
+int oz_chunks(int Np) { return ceil_div(Np, kOzChunk); }
 
 // Transposed slices of X (N x w): planes S x wp x Np, plane[s][c][r] = digit s of x_rc.
 // 32 x 32 tiles through shared memory so that reads and writes are both contiguous.
@@ -382,7 +389,7 @@ __global__ void oz_split_cols_t_kernel(int n, const double* __restrict__ X, int 
     if (c >= wp || r >= Np) continue;
     const double a = tile[tx][i];
     int d[kOzS];
-    oz_digits(oz_fixed(a, c < w ? E[c] : 0), d);
+    oz_digits(oz_fixed(a, c < w ? E[(size_t)(r / kOzChunk) * wp + c] : 0), d);
     const bool neg = a < 0.0;
 #pragma unroll
     for (int s = 0; s < kOzS; ++s) P[s * plane + (size_t)c * Np + r] = oz_bf16(d[s], neg);
@@ -393,7 +400,8 @@ size_t ozaki_tn_work_bytes(int n, int ka, int kb) {
   const size_t Np = (size_t)round_up(n, kOzBK);
   const size_t kap = (size_t)round_up(ka, kOzBM), kbp = (size_t)round_up(kb, kOzBN);
   const size_t splits = 4 * kSMs;
-  return kOzS * (kap + kbp) * Np * sizeof(__nv_bfloat16) + (kap + kbp) * sizeof(int) +
+  return kOzS * (kap + kbp) * Np * sizeof(__nv_bfloat16) +
+         (kap + kbp) * (size_t)oz_chunks((int)Np) * sizeof(int) +
          splits * (size_t)ka * kb * sizeof(double) + 4096;
 }
 
@@ -405,14 +413,14 @@ cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, in
   char* w = static_cast<char*>(work);
   __nv_bfloat16* PA = reinterpret_cast<__nv_bfloat16*>(w);
   __nv_bfloat16* PB = PA + (size_t)kOzS * kap * Np;
+  const int nch = oz_chunks(Np);
   int* EA = reinterpret_cast<int*>(PB + (size_t)kOzS * kbp * Np);
-  int* EB = EA + kap;
+  int* EB = EA + (size_t)kap * nch;
+  int* Eend = EB + (size_t)kbp * nch;
   double* partial = reinterpret_cast<double*>(
-      reinterpret_cast<char*>(EB + kbp) + (256 - (reinterpret_cast<uintptr_t>(EB + kbp) & 255)));
-  oz_fill_int_kernel<<<1, 256, 0, st>>>(EA, kap + kbp, -100000); note_launch();
-  oz_col_exp_kernel<<<std::min(ceil_div(n, 64), 4 * kSMs), 256, 0, st>>>(n, A, lda, ka, EA); note_launch();
-  oz_col_exp_kernel<<<std::min(ceil_div(n, 64), 4 * kSMs), 256, 0, st>>>(n, B, ldb, kb, EB); note_launch();
-  oz_clamp_exp_kernel<<<1, 256, 0, st>>>(EA, kap + kbp); note_launch();
+      reinterpret_cast<char*>(Eend) + (256 - (reinterpret_cast<uintptr_t>(Eend) & 255)));
+  oz_col_exp_kernel<<<dim3(nch, ceil_div(ka, 32)), 256, 0, st>>>(n, A, lda, ka, kap, 0, EA); note_launch();
+  oz_col_exp_kernel<<<dim3(nch, ceil_div(kb, 32)), 256, 0, st>>>(n, B, ldb, kb, kbp, 0, EB); note_launch();
   dim3 ga(ceil_div(Np, 32), ceil_div(kap, 32));
   oz_split_cols_t_kernel<<<ga, 256, 0, st>>>(n, A, lda, ka, Np, kap, EA, PA); note_launch();
   dim3 gb(ceil_div(Np, 32), ceil_div(kbp, 32));
@@ -421,8 +429,8 @@ cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, in
   const int tiles = (kap / kOzBM) * (kbp / kOzBN);
   const int nk = Np / kOzBK;
   int nsplit = std::max(1, std::min(4 * kSMs, (2 * kSMs + tiles - 1) / tiles));
-  int k_split = ceil_div(nk, nsplit);
-  k_split = round_up(k_split, kOzFlush) > nk ? k_split : round_up(k_split, kOzFlush);
+  // splits start on chunk boundaries (the chunk exponents apply per fold)
+  const int k_split = round_up(ceil_div(nk, nsplit), kOzFlush);
   nsplit = ceil_div(nk, k_split);
   dim3 grid(kap / kOzBM, kbp / kOzBN, nsplit);
   cudaError_t e =
@@ -449,7 +457,8 @@ cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int 
 }
 
 // Transposed column slices of A's w columns into rows [c0, c0 + w) of planes S x cap x Np,
-// exponents into E[c0 .. c0 + w).  Rows of the planes outside [c0, c0 + w) are untouched.
+// chunk exponents into E[ch * cap + c0 .. + w) for every 1024-row chunk ch < oz_chunks(Np).
+// Rows of the planes outside [c0, c0 + w) are untouched.
 __global__ void oz_split_cols_t_off_kernel(int n, const double* __restrict__ X, int ldx, int w, int Np,
                                            int cap, int c_off, const int* __restrict__ E,
                                            __nv_bfloat16* __restrict__ P) {
@@ -467,7 +476,7 @@ __global__ void oz_split_cols_t_off_kernel(int n, const double* __restrict__ X, 
     if (c >= w || r >= Np) continue;
     const double a = tile[tx][i];
     int d[kOzS];
-    oz_digits(oz_fixed(a, E[c_off + c]), d);
+    oz_digits(oz_fixed(a, E[(size_t)(r / kOzChunk) * cap + c_off + c]), d);
     const bool neg = a < 0.0;
 #pragma unroll
     for (int s = 0; s < kOzS; ++s) P[s * plane + (size_t)(c_off + c) * Np + r] = oz_bf16(d[s], neg);
@@ -478,9 +487,8 @@ cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, in
                             int c_off, void* planes, int* E) {
   if (w <= 0) return cudaSuccess;
   __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
-  oz_fill_int_kernel<<<1, 256, 0, st>>>(E + c_off, w, -100000); note_launch();
-  oz_col_exp_kernel<<<std::min(ceil_div(n, 64), 4 * kSMs), 256, 0, st>>>(n, A, lda, w, E + c_off); note_launch();
-  oz_clamp_exp_kernel<<<1, 256, 0, st>>>(E + c_off, w); note_launch();
+  oz_col_exp_kernel<<<dim3(oz_chunks(Np), ceil_div(w, 32)), 256, 0, st>>>(n, A, lda, w, cap, c_off,
+                                                                           E); note_launch();
   dim3 g(ceil_div(Np, 32), ceil_div(w, 32));
   oz_split_cols_t_off_kernel<<<g, 256, 0, st>>>(n, A, lda, w, Np, cap, c_off, E, P); note_launch();
   return cudaGetLastError();
@@ -498,7 +506,8 @@ __global__ void oz_zero_rows_kernel(__nv_bfloat16* P, size_t plane, int Np, int 
 }
 
 // out (ka x kb) = A^T B from transposed planes: rows [a0, a0 + ka) of PA (S x capA x Np,
-// exponents EA) and rows [0, kb) of PB (S x capB x Np, exponents EB; capB >= round_up(kb, 32)).
+// chunk exponents EA, stride capA) and rows [0, kb) of PB (S x capB x Np, chunk exponents EB,
+// stride capB; capB >= round_up(kb, 32)).
 cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const int* EA, int capA,
                                 int a0, int ka, const void* PB, const int* EB, int capB, int kb,
                                 double* out, double* partial) {
@@ -509,7 +518,7 @@ cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const i
   const int tiles = mt * nt;
   const int nk = Np / kOzBK;
   int nsplit = std::max(1, std::min(4 * kSMs, (2 * kSMs + tiles - 1) / tiles));
-  const int k_split = ceil_div(nk, nsplit);
+  const int k_split = round_up(ceil_div(nk, nsplit), kOzFlush);   // chunk-aligned splits
   nsplit = ceil_div(nk, k_split);
   dim3 grid(mt, nt, nsplit);
   // the planes of A are read through an offset base: their row count per plane stays capA

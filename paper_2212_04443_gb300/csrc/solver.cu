@@ -60,6 +60,31 @@ struct Timer {
   }
 };
 
+// Long-row schedule of A (rows with more than kLongRow nonzeros become segments), with
+// segment workspace for products up to width_bytes per row.  Rebuilt on every call: it costs
+// one pass over rowptr and one host synchronisation.
+bchdav_status prepare_long_rows(bchdav_handle h, const bchdav_csr* A, size_t width_bytes) {
+  cudaStream_t st = h->stream;
+  const int n = A->n;
+  h->lg = bchdav::SpmmLong();
+  const long long cap = spmm_long_seg_cap(A->nnz);
+  BCHDAV_TRY(h->ensure(h->lg_cnt, (size_t)n * sizeof(int)));
+  BCHDAV_TRY(h->ensure(h->lg_off, (size_t)(n + 1) * sizeof(long long)));
+  BCHDAV_TRY(h->ensure(h->lg_tiles, (size_t)scan_tile_count(n) * sizeof(long long) + 64));
+  BCHDAV_TRY(h->ensure(h->lg_row, (size_t)cap * sizeof(int)));
+  long long total = 0, n_seg = 0;
+  HCUDA(build_spmm_long(st, n, A->rowptr, h->lg_cnt.as<int>(), h->lg_off.as<long long>(),
+                        h->lg_tiles.as<long long>(), h->lg_row.as<int>(), cap, &total, &n_seg));
+  if (n_seg > 0) {
+    BCHDAV_TRY(h->ensure(h->lg_pseg, (size_t)n_seg * width_bytes));
+    h->lg.n_seg = n_seg;
+    h->lg.seg_off = h->lg_off.as<long long>();
+    h->lg.seg_row = h->lg_row.as<int>();
+    h->lg.pseg = h->lg_pseg.p;
+  }
+  return BCHDAV_OK;
+}
+
 // ---------------- Algorithm 3 ----------------
 // Y = p_m(A) X.  prec MIXED: recurrence in float32 (val32 required).
 bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val32, const double* X,
@@ -81,7 +106,8 @@ bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val3
     HCUDA(launch_f64_to_f32(st, n, b, X, ldx, T[0], ldb));
     // step 1: U = (A X - c X) sigma / e
     HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[0], ldb, b, T[1], ldb,
-                                   nullptr, 0, (float)(sigma / e), (float)(-c * sigma / e), 0.f));
+                                   nullptr, 0, (float)(sigma / e), (float)(-c * sigma / e), 0.f,
+                                   nullptr, 0, nullptr, h->long_rows()));
     bytes += csr_bytes + 3.0 * n * b * sx;
     int prev = 0, cur = 1;
     for (int i = 2; i <= m; ++i) {
@@ -90,7 +116,8 @@ bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val3
       while (nxt == prev || nxt == cur) ++nxt;
       HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[cur], ldb, b, T[nxt],
                                      ldb, T[prev], ldb, (float)(2.0 * sigma1 / e),
-                                     (float)(-2.0 * sigma1 * c / e), (float)(-sigma * sigma1)));
+                                     (float)(-2.0 * sigma1 * c / e), (float)(-sigma * sigma1),
+                                     nullptr, 0, nullptr, h->long_rows()));
       bytes += csr_bytes + 4.0 * n * b * sx;
       prev = cur;
       cur = nxt;
@@ -105,7 +132,8 @@ bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val3
     double* out = (m == 1) ? Y : T[0];
     int outld = (m == 1) ? ldy : ldb;
     HCUDA(launch_spmm_axpby<double>(st, n, A->rowptr, A->colidx, A->val, X, ldx, b, out, outld,
-                                    nullptr, 0, sigma / e, -c * sigma / e, 0.0));
+                                    nullptr, 0, sigma / e, -c * sigma / e, 0.0, nullptr, 0, nullptr,
+                                    h->long_rows()));
     bytes += csr_bytes + 3.0 * n * b * sx;
     const double* curp = out;
     int curld = outld;
@@ -124,7 +152,8 @@ bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val3
       }
       HCUDA(launch_spmm_axpby<double>(st, n, A->rowptr, A->colidx, A->val, curp, curld, b, nxt,
                                       nxtld, prevp, prevld, 2.0 * sigma1 / e,
-                                      -2.0 * sigma1 * c / e, -sigma * sigma1));
+                                      -2.0 * sigma1 * c / e, -sigma * sigma1, nullptr, 0, nullptr,
+                                      h->long_rows()));
       bytes += csr_bytes + 4.0 * n * b * sx;
       prevp = curp;
       prevld = curld;
@@ -203,7 +232,7 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
   double bytes = 0.0;
   HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[0], ldb, b, T[1], ldb,
                                  nullptr, 0, (float)(sigma1 / e), (float)(-c * sigma1 / e), 0.f, Rp,
-                                 ldb, delta_d));
+                                 ldb, delta_d, h->long_rows()));
   bytes += csr_bytes + (any_res ? 4.0 : 3.0) * n * b * 4.0;
   int prev = 0, cur = 1;
   for (int i = 2; i <= m; ++i) {
@@ -212,7 +241,7 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
     HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[cur], ldb, b, T[nxt], ldb,
                                    T[prev], ldb, (float)(2.0 * sig[i] / e),
                                    (float)(-2.0 * sig[i] * c / e), (float)(-sig[i - 1] * sig[i]),
-                                   Rp, ldb, delta_d + (size_t)(i - 1) * 64));
+                                   Rp, ldb, delta_d + (size_t)(i - 1) * 64, h->long_rows()));
     bytes += csr_bytes + (any_res ? 5.0 : 4.0) * n * b * 4.0;
     prev = cur;
     cur = nxt;
@@ -223,9 +252,30 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
 }
 
 // ---------------- Step 6 ----------------
+// Where the cached slices of V live: column planes of V (S x capV x Np, exponents after them) in
+// oz_vt and row planes (S x n x KpCap, exponents after them) in oz_vr.  Both are sized for the
+// largest subspace `cols` once, so that the exponent arrays stay at fixed offsets for every call.
+struct OzLayout {
+  int Np, capV, KpCap;
+  size_t vt_planes, vr_planes;
+};
+OzLayout oz_layout(int n, int cols) {
+  OzLayout L;
+  cols = std::max(cols, 1);
+  L.Np = oz_pad_k(n);
+  L.capV = oz_pad_rows(cols);
+  L.KpCap = oz_pad_k(cols);
+  L.vt_planes = oz_planes_bytes(L.capV, L.Np);
+  L.vr_planes = oz_planes_bytes(n, L.KpCap);
+  return L;
+}
+
+// cap_cols: number of V columns the cached planes must be able to hold (0: just k).
+// vt_valid (optional): on return, the number of leading columns of V whose column planes are
+// current in oz_vt (k when this call made them, else 0).
 bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, double* X, int ldx,
                        int b, uint64_t seed, double tau_dep, int64_t* rep_counter, int* n_rep,
-                       int dense_path = 0) {
+                       int dense_path = 0, int cap_cols = 0, int* vt_valid = nullptr) {
   cudaStream_t st = h->stream;
   if (b > 64) {
     h->set_error(BCHDAV_ERR_ARG, "block size b must be <= 64");
@@ -261,24 +311,26 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   *n_rep = 0;
   // tensor-core path: slices of V (by columns for V^T X, by rows for X -= V C) are made once
   // and serve both passes and every retry; X is sliced by columns for each Gram product
+  if (vt_valid) *vt_valid = 0;
   const bool tc = dense_path == 0 && ozaki_nn_supported(std::max(k, 1));
-  const int Np = oz_pad_k(n);
-  const int capV = oz_pad_rows(std::max(k, 1)), capX = oz_pad_cols(b);
+  const OzLayout L = oz_layout(n, std::max(k, cap_cols));
+  const int Np = L.Np, capV = L.capV, capX = oz_pad_cols(b);
   const int Kp = oz_pad_k(std::max(k, 1));
   int *Evt = nullptr, *Evr = nullptr, *Ext = nullptr;
   if (tc) {
-    BCHDAV_TRY(h->ensure(h->oz_vt, oz_planes_bytes(capV, Np) + capV * sizeof(int) + 256));
-    BCHDAV_TRY(h->ensure(h->oz_vr, oz_planes_bytes(n, Kp) + (size_t)n * sizeof(int) + 256));
-    BCHDAV_TRY(h->ensure(h->oz_xt, oz_planes_bytes(capX, Np) + capX * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_vt, L.vt_planes + (size_t)oz_chunks(Np) * capV * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_vr, L.vr_planes + (size_t)n * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_xt, oz_planes_bytes(capX, Np) +
+                                       (size_t)oz_chunks(Np) * capX * sizeof(int) + 256));
     BCHDAV_TRY(h->ensure(h->oz_bw, oz_bwork_bytes(std::max(k, b), std::max(b, 64))));
     BCHDAV_TRY(h->ensure(h->oz_part, (size_t)4 * kSMs * std::max(k, b) * b * sizeof(double)));
-    BCHDAV_TRY(h->ensure(h->oz, ozaki_nn_work_bytes(n, b, b)));
-    Evt = reinterpret_cast<int*>(h->oz_vt.as<char>() + oz_planes_bytes(capV, Np));
-    Evr = reinterpret_cast<int*>(h->oz_vr.as<char>() + oz_planes_bytes(n, Kp));
+    Evt = reinterpret_cast<int*>(h->oz_vt.as<char>() + L.vt_planes);
+    Evr = reinterpret_cast<int*>(h->oz_vr.as<char>() + L.vr_planes);
     Ext = reinterpret_cast<int*>(h->oz_xt.as<char>() + oz_planes_bytes(capX, Np));
     if (k > 0) {
       HCUDA(oz_slice_cols_t(st, n, V, ldv, k, Np, capV, 0, h->oz_vt.p, Evt));
       HCUDA(oz_slice_rows(st, n, V, ldv, k, Kp, h->oz_vr.p, Evr));
+      if (vt_valid) *vt_valid = k;
     }
   }
   double* Gd = h->G.as<double>();
@@ -435,8 +487,9 @@ bchdav_status bchdav_spmm(bchdav_handle h, const bchdav_csr* A, const double* X,
     h->set_error(BCHDAV_ERR_ARG, "spmm: bad block arguments");
     return BCHDAV_ERR_ARG;
   }
+  BCHDAV_TRY(prepare_long_rows(h, A, (size_t)b * sizeof(double)));
   HCUDA(launch_spmm_axpby<double>(h->stream, A->n, A->rowptr, A->colidx, A->val, X, ldx, b, Y, ldy,
-                                  nullptr, 0, 1.0, 0.0, 0.0));
+                                  nullptr, 0, 1.0, 0.0, 0.0, nullptr, 0, nullptr, h->long_rows()));
   return BCHDAV_OK;
 }
 
@@ -455,6 +508,7 @@ bchdav_status bchdav_filter(bchdav_handle h, const bchdav_csr* A, const double* 
     HCUDA(launch_f64_to_f32_vec(h->stream, A->nnz, A->val, h->val32.as<float>()));
     v32 = h->val32.as<float>();
   }
+  BCHDAV_TRY(prepare_long_rows(h, A, (size_t)b * sizeof(double)));
   return run_filter(h, A, v32, X, ldx, b, m, a, upb, a0, precision, Y, ldy, nullptr);
 }
 
@@ -594,16 +648,25 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   BCHDAV_TRY(h->ensure(h->G, (size_t)std::max(ncols * b, 64) * sizeof(double)));
   BCHDAV_TRY(h->ensure_pinned((size_t)std::max(4 * act_max + 4 * ncols, 1024)));
   BCHDAV_TRY(h->ensure_aux((size_t)(m + 1) * 64 + 256));
-  if (opts.dense_path == 0)
-    BCHDAV_TRY(h->ensure(h->oz, std::max({ozaki_nn_work_bytes(N, std::min(ncols, 448), act_max),
-                                          ozaki_nn_work_bytes(N, std::min(ncols, 448), b),
-                                          ozaki_tn_work_bytes(N, ncols, b)})));
+  // tensor-core products: V's column planes (Steps 6, 8) and row planes (Steps 6, 11) sized for
+  // the whole subspace, X / W column planes, the split-B work and the split-reduction partials
+  const OzLayout OL = oz_layout(N, ncols);
+  if (opts.dense_path == 0) {
+    BCHDAV_TRY(h->ensure(h->oz_vt, OL.vt_planes + (size_t)oz_chunks(OL.Np) * OL.capV * sizeof(int) +
+                                       256));
+    BCHDAV_TRY(h->ensure(h->oz_vr, OL.vr_planes + (size_t)N * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_xt, oz_planes_bytes(oz_pad_cols(b), OL.Np) +
+                                       (size_t)oz_chunks(OL.Np) * oz_pad_cols(b) * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_bw, oz_bwork_bytes(std::max(ncols, act_max), std::max(act_max, 64))));
+    BCHDAV_TRY(h->ensure(h->oz_part, (size_t)4 * kSMs * ncols * b * sizeof(double)));
+  }
   const float* val32 = A->val_f32;
   if (prec == BCHDAV_PREC_MIXED && !val32) {
     BCHDAV_TRY(h->ensure(h->val32, (size_t)A->nnz * sizeof(float)));
     HCUDA(launch_f64_to_f32_vec(st, A->nnz, A->val, h->val32.as<float>()));
     val32 = h->val32.as<float>();
   }
+  BCHDAV_TRY(prepare_long_rows(h, A, (size_t)std::max(2 * b, 64) * sizeof(double)));
   double* V = h->V.as<double>();
   double* W = h->W.as<double>();
   double* Vtmp = h->Vtmp.as<double>();
@@ -680,15 +743,16 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     tm_orth.start(st);
     int nrep = 0;
     const int k_orth = k_sub;
+    int vt_valid = 0;
     BCHDAV_TRY(run_orth(h, N, V, ldv, k_sub, Xo, ldb, b, opts.seed, tau_dep, &rep_counter, &nrep,
-                        opts.dense_path));
+                        opts.dense_path, ncols, &vt_valid));
     n_rep_total += nrep;
     HCUDA(launch_copy_block(st, N, b, Xo, ldb, V + k_sub, ldv));
     tm_orth.stop(st);
     // Step 7: W(:, k_act+1 : k_act+b) = A V_new
     tm_spmm.start(st);
     HCUDA(launch_spmm_axpby<double>(st, N, A->rowptr, A->colidx, A->val, Xo, ldb, b, W, ldb,
-                                    nullptr, 0, 1.0, 0.0, 0.0));
+                                    nullptr, 0, 1.0, 0.0, 0.0, nullptr, 0, nullptr, h->long_rows()));
     tm_spmm.stop(st);
     ++n_spmm;
     k_act += b;
@@ -696,7 +760,17 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     // Step 8: H(1:k_act, new) = V(:, k_c+1:k_sub)^T W_new, symmetrise
     tm_h.start(st);
     if (opts.dense_path == 0) {
-      HCUDA(launch_ozaki_tn(st, N, V + k_c, ldv, k_act, W, ldb, b, h->G.as<double>(), h->oz.p));
+      // V's column planes from Step 6 are still current for columns [0, vt_valid); slice the
+      // rest of V(:, k_c+1:k_sub) (the new block) and W_new, then reduce over the N rows
+      int* Evt = reinterpret_cast<int*>(h->oz_vt.as<char>() + OL.vt_planes);
+      const int capX = oz_pad_cols(b);
+      int* Ext = reinterpret_cast<int*>(h->oz_xt.as<char>() + oz_planes_bytes(capX, OL.Np));
+      const int c_from = std::max(vt_valid, k_c);
+      HCUDA(oz_slice_cols_t(st, N, V + c_from, ldv, k_sub - c_from, OL.Np, OL.capV, c_from,
+                            h->oz_vt.p, Evt));
+      HCUDA(oz_slice_cols_t(st, N, W, ldb, b, OL.Np, capX, 0, h->oz_xt.p, Ext));
+      HCUDA(oz_gram_from_planes(st, OL.Np, h->oz_vt.p, Evt, OL.capV, k_c, k_act, h->oz_xt.p, Ext,
+                                capX, b, h->G.as<double>(), h->oz_part.as<double>()));
     } else {
       HCUDA(launch_gemm_tn_partial(st, N, V + k_c, ldv, k_act, W, ldb, b, h->part.as<double>(),
                                    chunks));
@@ -721,8 +795,13 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     // Step 11: rotation V(:, k_c+1 : k_c+k_act) = V(:, k_c+1 : k_c+k_old) Y(:, 1:k_act)
     tm_rot.start(st);
     if (opts.dense_path == 0 && ozaki_nn_supported(k_old)) {
-      HCUDA(launch_ozaki_nn(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act, V + k_c, ldv, false,
-                            h->oz.p));
+      // the row planes of Step 6 are stale (V gained a block); re-slice V(:, k_c+1:k_c+k_old)
+      // into the same buffer, then V is overwritten in place (the planes hold all of A)
+      int* Evr = reinterpret_cast<int*>(h->oz_vr.as<char>() + OL.vr_planes);
+      const int Kp = oz_pad_k(k_old);
+      HCUDA(oz_slice_rows(st, N, V + k_c, ldv, k_old, Kp, h->oz_vr.p, Evr));
+      HCUDA(oz_nn_from_planes(st, N, k_old, Kp, h->oz_vr.p, Evr, Ym, act_max, k_act, V + k_c, ldv,
+                              false, h->oz_bw.p));
     } else {
       HCUDA(launch_gemm_nn_inplace(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act));
     }
@@ -737,7 +816,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     int nparts = 0;
     HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c, ldv, nres, Dd,
                             h->part.as<double>(), &nparts,
-                            prec == BCHDAV_PREC_MIXED ? h->Rres.as<double>() : nullptr, ldr));
+                            prec == BCHDAV_PREC_MIXED ? h->Rres.as<double>() : nullptr, ldr,
+                            h->long_rows()));
     HCUDA(launch_reduce_partials(st, h->part.as<double>(), nparts, 2 * nres, dsel, 1.0));
     HCUDA(cudaMemcpyAsync(hp + act_max + 1, dsel, 2 * nres * sizeof(double), cudaMemcpyDeviceToHost,
                           st));
@@ -874,7 +954,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       int w = std::min(64, n_out - c0);
       int np = 0;
       HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, evecs + c0, k, w, evals + c0,
-                              h->part.as<double>(), &np));
+                              h->part.as<double>(), &np, nullptr, 0, h->long_rows()));
       HCUDA(launch_reduce_partials(st, h->part.as<double>(), np, 2 * w, dsel, 1.0));
       HCUDA(cudaMemcpyAsync(hp + 1024 - 128, dsel, 2 * w * sizeof(double), cudaMemcpyDeviceToHost, st));
       HCUDA(cudaStreamSynchronize(st));

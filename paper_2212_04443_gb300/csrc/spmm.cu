@@ -11,6 +11,8 @@
 // reads X and Z at the row itself and writes Y once: compulsory bytes per
 // launch are 4 (N + 1) + nnz (4 + sizeof(T)) + N b sizeof(T) (gathered X
 // counted once) + 2 N b sizeof(T) (Z and Y).
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace bchdav {
@@ -79,22 +81,142 @@ __device__ __forceinline__ void row_product(const int* __restrict__ colidx, cons
   }
 }
 
+// ---------------- long rows: fixed-size segments, reduced in a fixed order ----------------
+// A row with more than kLongRow nonzeros would keep one row group busy for its whole length
+// (power-law graphs have rows of 10^5 entries), so such rows are cut into segments of kLongRow
+// nonzeros.  One CTA computes each segment's partial product into pseg (segment-major, b
+// values); the row kernel then adds a long row's segments in segment order.  Both sums run in
+// a fixed order: results do not depend on scheduling.
+__global__ void long_count_segments_kernel(int n, const int* __restrict__ rowptr,
+                                           int* __restrict__ cnt) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int len = rowptr[r + 1] - rowptr[r];
+    cnt[r] = len > kLongRow ? (len + kLongRow - 1) / kLongRow : 0;
+  }
+}
+
+__global__ void long_fill_rows_kernel(int n, const long long* __restrict__ seg_off,
+                                      int* __restrict__ seg_row) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    for (long long s = seg_off[r]; s < seg_off[r + 1]; ++s) seg_row[s] = r;
+}
+
+cudaError_t build_spmm_long(cudaStream_t st, int n, const int* rowptr, int* cnt_work,
+                            long long* seg_off, long long* tile_sums, int* seg_row,
+                            long long seg_cap, long long* host_total, long long* n_seg) {
+  *n_seg = 0;
+  if (n <= 0) return cudaSuccess;
+  const int grid = std::min(ceil_div(n, 256), 16 * kSMs);
+  long_count_segments_kernel<<<grid, 256, 0, st>>>(n, rowptr, cnt_work); note_launch();
+  cudaError_t e = exclusive_scan(st, n, cnt_work, 0, seg_off, tile_sums);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(host_total, seg_off + n, sizeof(long long), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  if (*host_total > seg_cap) return cudaErrorInvalidValue;
+  *n_seg = *host_total;
+  if (*n_seg > 0) {
+    long_fill_rows_kernel<<<grid, 256, 0, st>>>(n, seg_off, seg_row); note_launch();
+  }
+  return cudaGetLastError();
+}
+
+long long spmm_long_seg_cap(long long nnz) { return 2 * (nnz / kLongRow) + 1; }
+
+// One CTA per segment: the segment's colidx/val are staged in shared memory by all threads
+// (independent loads), then G row groups of tpr threads each gather every G-th entry; the
+// group sums are added in group order.
+template <typename T, int VW>
+__global__ void __launch_bounds__(256) spmm_long_seg_kernel(
+    const int* __restrict__ rowptr, const int* __restrict__ colidx, const T* __restrict__ val,
+    const T* __restrict__ X, int ldx, int b, int tpr, const long long* __restrict__ seg_off,
+    const int* __restrict__ seg_row, T* __restrict__ pseg, int ldp) {
+  __shared__ int s_col[kLongRow];
+  __shared__ T s_val[kLongRow];
+  __shared__ T s_red[256 * VW];
+  const long long s = blockIdx.x;
+  const int row = seg_row[s];
+  const long long q0 = rowptr[row] + (s - seg_off[row]) * (long long)kLongRow;
+  const int cnt = (int)min((long long)kLongRow, (long long)rowptr[row + 1] - q0);
+  for (int e = threadIdx.x; e < cnt; e += 256) {
+    s_col[e] = colidx[q0 + e];
+    s_val[e] = val[q0 + e];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gpw = 32 / tpr, g_lane = lane / tpr, li = lane - g_lane * tpr;
+  const int G = 8 * gpw, g = warp * gpw + g_lane;
+  T acc[VW];
+#pragma unroll
+  for (int i = 0; i < VW; ++i) acc[i] = T(0);
+  const int c0 = li * VW;
+  if (g_lane < gpw && c0 < b) {
+    int e = g;
+    for (; e + 3 * G < cnt; e += 4 * G) {
+      T x0[VW], x1[VW], x2[VW], x3[VW];
+      ldv<T, VW>(X + (size_t)s_col[e] * ldx + c0, x0);
+      ldv<T, VW>(X + (size_t)s_col[e + G] * ldx + c0, x1);
+      ldv<T, VW>(X + (size_t)s_col[e + 2 * G] * ldx + c0, x2);
+      ldv<T, VW>(X + (size_t)s_col[e + 3 * G] * ldx + c0, x3);
+      const T a0 = s_val[e], a1 = s_val[e + G], a2 = s_val[e + 2 * G], a3 = s_val[e + 3 * G];
+#pragma unroll
+      for (int i = 0; i < VW; ++i) {
+        acc[i] = fma(a0, x0[i], acc[i]);
+        acc[i] = fma(a1, x1[i], acc[i]);
+        acc[i] = fma(a2, x2[i], acc[i]);
+        acc[i] = fma(a3, x3[i], acc[i]);
+      }
+    }
+    for (; e < cnt; e += G) {
+      T x[VW];
+      ldv<T, VW>(X + (size_t)s_col[e] * ldx + c0, x);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) acc[i] = fma(s_val[e], x[i], acc[i]);
+    }
+  }
+  // s_red[g][column]: G groups x b columns (G * b <= 256 * VW)
+  if (g_lane < gpw && c0 < b) {
+#pragma unroll
+    for (int i = 0; i < VW; ++i)
+      if (c0 + i < b) s_red[g * b + c0 + i] = acc[i];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < b; c += 256) {
+    T t = T(0);
+    for (int q = 0; q < G; ++q) t += s_red[q * b + c];
+    pseg[s * ldp + c] = t;
+  }
+}
+
+// ---------------- row kernel ----------------
+// A group of tpr consecutive threads owns one row (groups may straddle warps); rpb rows per
+// CTA.  Rows longer than kLongRow read their segment sums instead of walking their nonzeros.
 template <typename T, int VW>
 __global__ void __launch_bounds__(256) spmm_axpby_kernel(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
     const T* __restrict__ val, const T* __restrict__ X, int ldx, int b, T* __restrict__ Y, int ldy,
     const T* __restrict__ Z, int ldz, T alpha, T beta, T gamma, const T* __restrict__ R, int ldr,
-    const T* __restrict__ delta, int tpr, int rpb) {
+    const T* __restrict__ delta, int tpr, int rpb, const long long* __restrict__ seg_off,
+    const T* __restrict__ pseg) {
   const int t = threadIdx.x;
   const int rl = t / tpr;
   if (rl >= rpb) return;
   const int row = blockIdx.x * rpb + rl;
   if (row >= n) return;
   const int c0 = (t - rl * tpr) * VW;
+  if (c0 >= b) return;   // VW == 1 only: b need not fill the group
   T acc[VW];
 #pragma unroll
   for (int i = 0; i < VW; ++i) acc[i] = T(0);
-  row_product<T, VW>(colidx, val, X, ldx, c0, __ldg(rowptr + row), __ldg(rowptr + row + 1), acc);
+  const int p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
+  if (seg_off != nullptr && p1 - p0 > kLongRow) {
+    for (long long s = seg_off[row]; s < seg_off[row + 1]; ++s)
+#pragma unroll
+      for (int i = 0; i < VW; ++i) acc[i] += pseg[s * b + c0 + i];
+  } else {
+    row_product<T, VW>(colidx, val, X, ldx, c0, p0, p1, acc);
+  }
   T out[VW];
 #pragma unroll
   for (int i = 0; i < VW; ++i) out[i] = alpha * acc[i];
@@ -119,29 +241,6 @@ __global__ void __launch_bounds__(256) spmm_axpby_kernel(
   stv<T, VW>(Y + (size_t)row * ldy + c0, out);
 }
 
-// VW = 1 variant with a ragged last group: any b, any alignment.
-template <typename T>
-__global__ void __launch_bounds__(256) spmm_axpby_scalar_kernel(
-    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-    const T* __restrict__ val, const T* __restrict__ X, int ldx, int b, T* __restrict__ Y, int ldy,
-    const T* __restrict__ Z, int ldz, T alpha, T beta, T gamma, const T* __restrict__ R, int ldr,
-    const T* __restrict__ delta, int tpr, int rpb) {
-  const int t = threadIdx.x;
-  const int rl = t / tpr;
-  if (rl >= rpb) return;
-  const int row = blockIdx.x * rpb + rl;
-  if (row >= n) return;
-  const int c0 = t - rl * tpr;
-  if (c0 >= b) return;
-  T acc[1] = {T(0)};
-  row_product<T, 1>(colidx, val, X, ldx, c0, __ldg(rowptr + row), __ldg(rowptr + row + 1), acc);
-  T out = alpha * acc[0];
-  if (beta != T(0)) out = fma(beta, __ldg(X + (size_t)row * ldx + c0), out);
-  if (Z != nullptr) out = fma(gamma, __ldg(Z + (size_t)row * ldz + c0), out);
-  if (R != nullptr) out = fma(__ldg(delta + c0), __ldg(R + (size_t)row * ldr + c0), out);
-  Y[(size_t)row * ldy + c0] = out;
-}
-
 template <typename T>
 static int pick_vw(int b, const void* p1, int ld1, const void* p2, int ld2, const void* p3, int ld3) {
   const int cand[3] = {(int)(16 / sizeof(T)), (int)(8 / sizeof(T)), 1};
@@ -157,44 +256,70 @@ static int pick_vw(int b, const void* p1, int ld1, const void* p2, int ld2, cons
   return 1;
 }
 
+template <typename T, int VW>
+static cudaError_t spmm_rows_launch(cudaStream_t st, int n, const int* rowptr, const int* colidx,
+                                    const T* val, const T* X, int ldx, int b, T* Y, int ldy,
+                                    const T* Z, int ldz, T alpha, T beta, T gamma, const T* R,
+                                    int ldr, const T* delta, int tpr, const SpmmLong* lg) {
+  const long long* seg_off = nullptr;
+  const T* pseg = nullptr;
+  if (lg != nullptr && lg->n_seg > 0) {
+    if (lg->n_seg > 0x7fffffffLL) return cudaErrorInvalidValue;
+    T* ps = static_cast<T*>(lg->pseg);
+    if (VW == 1) {
+      // one lane per column: at most 32 columns per pass
+      for (int c0 = 0; c0 < b; c0 += 32) {
+        const int w = std::min(32, b - c0);
+        spmm_long_seg_kernel<T, 1><<<(unsigned)lg->n_seg, 256, 0, st>>>(
+            rowptr, colidx, val, X + c0, ldx, w, w, lg->seg_off, lg->seg_row, ps + c0, b);
+        note_launch();
+      }
+    } else {
+      spmm_long_seg_kernel<T, VW><<<(unsigned)lg->n_seg, 256, 0, st>>>(
+          rowptr, colidx, val, X, ldx, b, tpr, lg->seg_off, lg->seg_row, ps, b); note_launch();
+    }
+    seg_off = lg->seg_off;
+    pseg = ps;
+  }
+  const int rpb = 256 / tpr;
+  const int grid = ceil_div(n, rpb);
+  spmm_axpby_kernel<T, VW><<<grid, rpb * tpr, 0, st>>>(n, rowptr, colidx, val, X, ldx, b, Y, ldy,
+                                                       Z, ldz, alpha, beta, gamma, R, ldr, delta,
+                                                       tpr, rpb, seg_off, pseg); note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_spmm_axpby(cudaStream_t st, int n, const int* rowptr, const int* colidx,
                               const T* val, const T* X, int ldx, int b, T* Y, int ldy,
                               const T* Z, int ldz, T alpha, T beta, T gamma, const T* R, int ldr,
-                              const T* delta) {
+                              const T* delta, const SpmmLong* lg) {
   if (n <= 0 || b <= 0) return cudaSuccess;
   int vw = pick_vw<T>(b, X, ldx, Y, ldy, Z, ldz);
   if (R != nullptr && vw > 1 && (((uintptr_t)R % (vw * sizeof(T))) != 0 || ldr % vw != 0)) vw = 1;
-  int tpr = (b + vw - 1) / vw;
-  if (tpr > 256) return cudaErrorInvalidValue;
-  int rpb = 256 / tpr;
-  int threads = rpb * tpr;
-  int grid = ceil_div(n, rpb);
-  if (vw == 1) {
-    spmm_axpby_scalar_kernel<T><<<grid, threads, 0, st>>>(n, rowptr, colidx, val, X, ldx, b, Y,
-                                                          ldy, Z, ldz, alpha, beta, gamma, R, ldr, delta, tpr, rpb); note_launch();
-  } else if (vw == 2) {
-    spmm_axpby_kernel<T, 2><<<grid, threads, 0, st>>>(n, rowptr, colidx, val, X, ldx, b, Y, ldy,
-                                                      Z, ldz, alpha, beta, gamma, R, ldr, delta,
-                                                      tpr, rpb); note_launch();
-  } else {
-    if constexpr (sizeof(T) == 4) {
-      spmm_axpby_kernel<T, 4><<<grid, threads, 0, st>>>(n, rowptr, colidx, val, X, ldx, b, Y, ldy,
-                                                        Z, ldz, alpha, beta, gamma, R, ldr, delta,
-                                                      tpr, rpb); note_launch();
-    }
-  }
-  return cudaGetLastError();
+  const int tpr = (b + vw - 1) / vw;
+  if (tpr > 256 || (vw > 1 && tpr > 32)) return cudaErrorInvalidValue;
+  if (vw == 1)
+    return spmm_rows_launch<T, 1>(st, n, rowptr, colidx, val, X, ldx, b, Y, ldy, Z, ldz, alpha,
+                                  beta, gamma, R, ldr, delta, tpr, lg);
+  if (vw == 2)
+    return spmm_rows_launch<T, 2>(st, n, rowptr, colidx, val, X, ldx, b, Y, ldy, Z, ldz, alpha,
+                                  beta, gamma, R, ldr, delta, tpr, lg);
+  if constexpr (sizeof(T) == 4)
+    return spmm_rows_launch<T, 4>(st, n, rowptr, colidx, val, X, ldx, b, Y, ldy, Z, ldz, alpha,
+                                  beta, gamma, R, ldr, delta, tpr, lg);
+  return cudaErrorInvalidValue;
 }
 
 template cudaError_t launch_spmm_axpby<double>(cudaStream_t, int, const int*, const int*,
                                                const double*, const double*, int, int, double*,
                                                int, const double*, int, double, double, double,
-                                               const double*, int, const double*);
+                                               const double*, int, const double*,
+                                               const SpmmLong*);
 template cudaError_t launch_spmm_axpby<float>(cudaStream_t, int, const int*, const int*,
                                               const float*, const float*, int, int, float*, int,
                                               const float*, int, float, float, float, const float*,
-                                              int, const float*);
+                                              int, const float*, const SpmmLong*);
 
 // ---------------- residual norms (Step 12) ----------------
 constexpr int kResidThreads = 256;
@@ -203,7 +328,7 @@ __global__ void __launch_bounds__(kResidThreads) spmm_resid_kernel(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
     const double* __restrict__ val, const double* __restrict__ V, int ldv, int b,
     const double* __restrict__ d, double* __restrict__ partial, double* __restrict__ Rout,
-    int ldr) {
+    int ldr, const long long* __restrict__ seg_off, const double* __restrict__ pseg) {
   // one thread per (row, column); block covers rows_per_block rows of all b columns
   extern __shared__ double sh[];
   const int rpb = kResidThreads / b;
@@ -214,8 +339,12 @@ __global__ void __launch_bounds__(kResidThreads) spmm_resid_kernel(
   if (rl < rpb) {
     for (int row = blockIdx.x * rpb + rl; row < n; row += gridDim.x * rpb) {
       double acc[1] = {0.0};
-      row_product<double, 1>(colidx, val, V, ldv, c, __ldg(rowptr + row), __ldg(rowptr + row + 1),
-                             acc);
+      const int p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
+      if (seg_off != nullptr && p1 - p0 > kLongRow) {
+        for (long long s = seg_off[row]; s < seg_off[row + 1]; ++s) acc[0] += pseg[s * b + c];
+      } else {
+        row_product<double, 1>(colidx, val, V, ldv, c, p0, p1, acc);
+      }
       double v = __ldg(V + (size_t)row * ldv + c);
       double r = fma(-__ldg(d + c), v, acc[0]);
       if (Rout != nullptr) Rout[(size_t)row * ldr + c] = r;
@@ -249,12 +378,27 @@ int spmm_resid_max_parts(int n, int b) {
 cudaError_t launch_spmm_resid(cudaStream_t st, int n, const int* rowptr, const int* colidx,
                               const double* val, const double* V, int ldv, int b,
                               const double* d, double* partial, int* n_parts, double* Rout,
-                              int ldr) {
+                              int ldr, const SpmmLong* lg) {
   if (b > kResidThreads || b <= 0) return cudaErrorInvalidValue;
   int grid = spmm_resid_max_parts(n, b);
   *n_parts = grid;
+  const long long* seg_off = nullptr;
+  const double* pseg = nullptr;
+  if (lg != nullptr && lg->n_seg > 0) {
+    if (lg->n_seg > 0x7fffffffLL) return cudaErrorInvalidValue;
+    double* ps = static_cast<double*>(lg->pseg);
+    // segment products of A V in column chunks of at most 32 (one lane per column)
+    for (int c0 = 0; c0 < b; c0 += 32) {
+      const int w = std::min(32, b - c0);
+      spmm_long_seg_kernel<double, 1><<<(unsigned)lg->n_seg, 256, 0, st>>>(
+          rowptr, colidx, val, V + c0, ldv, w, w, lg->seg_off, lg->seg_row, ps + c0, b);
+      note_launch();
+    }
+    seg_off = lg->seg_off;
+    pseg = ps;
+  }
   spmm_resid_kernel<<<grid, kResidThreads, 2 * kResidThreads * sizeof(double), st>>>(
-      n, rowptr, colidx, val, V, ldv, b, d, partial, Rout, ldr); note_launch();
+      n, rowptr, colidx, val, V, ldv, b, d, partial, Rout, ldr, seg_off, pseg); note_launch();
   return cudaGetLastError();
 }
 

@@ -102,6 +102,21 @@ def test_dense_brute_force(H):
         assert np.abs(ev - np.linalg.eigvalsh(L.dense())[:8]).max() < 1e-10
 
 
+def test_long_rows_solve_matches_brute_force(H):
+    """Hub rows over the SpMM segment length in every product of the solve (filter, A V,
+    residuals, final check), both precisions."""
+    g = synth.disjoint_union(synth.star_edges(3000), synth.rmat_edges(11, seed=4),
+                             synth.sbm_edges(1500, 3, d_in=8, d_out=1, seed=2))
+    L = oracle_csr(g)
+    assert np.diff(L.rowptr).max() > 2 * 1024
+    ref = np.linalg.eigvalsh(L.dense())
+    for prec in (0, 1):
+        ev, V, info, _ = gpu_solve(H, g, 10, 5, 11, 30, precision=prec)
+        assert info.status == 0
+        check_pairs(L, ev, V, 10)
+        assert np.abs(ev - ref[:10]).max() < 1e-10
+
+
 def test_union_zero_multiplicity_and_membership(H):
     g = synth.disjoint_union(synth.cycle_edges(30), synth.path_edges(25), synth.complete_edges(12),
                              synth.hypercube_edges(4), synth.star_edges(9))

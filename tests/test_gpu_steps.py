@@ -80,6 +80,46 @@ def test_spmm_matches_scipy(H, b):
     assert np.abs(Y - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
+def _hub_graph():
+    """Rows far over the 1024-nonzero segment length (star hubs of 5000 and 2500 leaves, whose
+    lengths are not multiples of it) next to power-law and short rows."""
+    return synth.disjoint_union(synth.star_edges(5000), synth.rmat_edges(12, seed=9),
+                                synth.star_edges(2500), synth.path_edges(40))
+
+
+@pytest.mark.parametrize("b", [1, 3, 8, 20, 33])
+def test_spmm_long_rows_match_scipy(H, b):
+    """Segmented rows: error within the float64 bound for a sum of len(row) products."""
+    import torch
+    g = _hub_graph()
+    A = device_csr(H, g)
+    L = oracle_csr(g)
+    assert np.diff(L.rowptr).max() > 4 * 1024
+    X = synth.gaussian_block(g.n, b, 11)
+    Y = to_np(H.spmm(A, torch.from_numpy(X).cuda()))
+    S = L.scipy()
+    ref = S @ X
+    bound = abs(S) @ np.abs(X)
+    lens = np.diff(L.rowptr)[:, None]
+    assert np.all(np.abs(Y - ref) <= 2 * lens * 2.0 ** -53 * bound + 1e-300)
+
+
+def test_filter_f32_long_rows(H):
+    import torch
+    import paper_2212_04443_gb300 as P
+    g = _hub_graph()
+    A = device_csr(H, g)
+    L = oracle_csr(g)
+    m, a, b = 11, 0.05, 16
+    X = synth.gaussian_block(g.n, b, 12)
+    Y = to_np(H.filter(A, torch.from_numpy(X).cuda(), m, a, 2.0, 0.0, precision=P.PREC_MIXED))
+    Yd = to_np(H.filter(A, torch.from_numpy(X).cuda(), m, a, 2.0, 0.0))
+    ref = oracle.chebyshev_filter(L.scipy(), X, m, a, 2.0, 0.0)
+    assert np.abs(Yd - ref).max() <= 1e-12 * np.abs(ref).max()
+    # float32 sums over hub rows of 5000 terms: a wider (length-proportional) bound
+    assert np.abs(Y - ref).max() <= 5000 * m * 2.0 ** -24 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("m,a,b", [(1, 0.3, 4), (11, 0.002, 5), (15, 0.55, 20), (13, 0.2, 10),
                                    (7, 1.1, 3)])
 def test_filter_f64_matches_oracle(H, m, a, b):
@@ -240,3 +280,30 @@ def test_gram_matches_float64(H, n, ka, kb, path):
     # rounded 48-bit split: |err_pq| <= n 2^-46 max|A_p| max|B_q| (+ float64 summation)
     bound = n * 2.0 ** -45 * np.abs(A).max(0)[:, None] * np.abs(B).max(0)[None, :]
     assert np.all(np.abs(out - ref) <= bound + 1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_gram_per_chunk_precision_with_hub_entries(H, path):
+    """A^T B where one row dwarfs the rest of its column (a hub vertex).  The split scales each
+    1024-row chunk by its own column exponent: with the hub alone in its chunk, the other rows
+    keep their 48 bits.  One exponent for the whole column (2^21) would round every other entry
+    to 2^-27 and leave an error near sqrt(n) 2^-28 ~ 1e-6 in that column of the product."""
+    import torch
+    n, ka, kb = 70001, 40, 12
+    rng = synth.rng(77)
+    A = rng.standard_normal((n, ka))
+    B = rng.standard_normal((n, kb))
+    A[:1024, 2] = 0.0
+    A[17, 2] = 2.0 ** 20
+    ref = A.T @ B
+    out = to_np(H.gram(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), dense_path=path))
+    fp = 4 * n * 2.0 ** -53 * (np.abs(A).T @ np.abs(B))     # float64 summation of either side
+    err = np.abs(out - ref)
+    ch = 1024
+    bound = np.zeros((ka, kb))
+    for r0 in range(0, n, ch):
+        a = np.abs(A[r0:r0 + ch]).max(0)
+        b = np.abs(B[r0:r0 + ch]).max(0)
+        bound += min(ch, n - r0) * 2.0 ** -45 * a[:, None] * b[None, :]
+    assert np.all(err <= bound + fp)
+    assert np.all(err[2] <= 1e-3 * np.sqrt(n) * 2.0 ** -28 + fp[2])
