@@ -91,6 +91,8 @@ typedef struct {
   double filter_bytes;      /* algorithmic bytes moved by all filter SpMM steps */
   double filter_ms_kernels; /* device time of those steps alone (CUDA events) */
   int64_t n_kernel_launches;/* kernels this library launched during the solve */
+  int32_t status;           /* the solve's return status (set by bchdav_solve_batched) */
+  int32_t reserved2;
 } bchdav_info;
 
 /* One record per outer iteration when opts.record_history is set. */
@@ -155,6 +157,27 @@ bchdav_status bchdav_solve_host(bchdav_handle h, int32_t n, int64_t nnz, const i
                                 const int32_t* colidx, const double* val, int32_t k, int32_t b,
                                 int32_t m, int32_t act_max, double tol, const bchdav_opts* opts,
                                 double* evals_host, double* evecs_host, bchdav_info* info);
+
+/* Many independent problems (the paper solves one; running many side by side is an
+ * extension of Algorithm 2, not a step of it).  Graph i is solved as by bchdav_solve with
+ * k[i], b[i], m[i], act_max[i] (0 = default), the shared tol and opts, except that
+ * opts->v_init is ignored and graph i draws its start block with seed opts->seed + i.
+ * evals[i] (k[i] doubles) and evecs[i] (N_i x k[i], ld = k[i]) are device arrays.
+ * The graphs run on a pool of worker handles, each with its own stream, taking graphs
+ * largest-first (nnz * b); the call returns when all are done.  infos[i] (status included)
+ * and per_graph_ms[i] (wall time of graph i's own solve) may be NULL arrays.  Returns
+ * BCHDAV_OK when every graph converged, else the first error, else BCHDAV_NOT_CONVERGED. */
+bchdav_status bchdav_solve_batched(bchdav_handle h, int32_t n_graphs, const bchdav_csr* As,
+                                   const int32_t* k, const int32_t* b, const int32_t* m,
+                                   const int32_t* act_max, double tol, const bchdav_opts* opts,
+                                   double* const* evals, double* const* evecs,
+                                   bchdav_info* infos, float* per_graph_ms);
+
+/* Kernels this library has launched in the process so far (all handles). */
+int64_t bchdav_launch_count(void);
+
+/* Number of concurrent solves of bchdav_solve_batched (default 8, 1..64). */
+bchdav_status bchdav_set_batch_workers(bchdav_handle h, int32_t n_workers);
 
 /* Per-iteration records of the last solve of this handle (opts.record_history). */
 int32_t bchdav_history(bchdav_handle h, bchdav_iter_record* out, int32_t max_records);

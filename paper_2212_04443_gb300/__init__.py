@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 __all__ = [
     "lib", "build", "Handle", "DeviceCSR", "BchdavError", "SolveInfo", "IterRecord",
-    "PREC_FP64", "PREC_MIXED", "EXPORTED_SYMBOLS",
+    "PREC_FP64", "PREC_MIXED", "EXPORTED_SYMBOLS", "launch_count",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -33,8 +33,14 @@ EXPORTED_SYMBOLS = [
     "bchdav_last_error", "bchdav_build_laplacian", "bchdav_free_csr", "bchdav_copy_csr", "bchdav_check_csr",
     "bchdav_solve", "bchdav_solve_host", "bchdav_history", "bchdav_filter", "bchdav_spmm",
     "bchdav_orthonormalize", "bchdav_gram", "bchdav_rotate", "bchdav_eigh",
-    "bchdav_eigh_noalloc",
+    "bchdav_eigh_noalloc", "bchdav_solve_batched", "bchdav_set_batch_workers",
+    "bchdav_launch_count",
 ]
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().bchdav_launch_count())
 
 
 class BchdavError(RuntimeError):
@@ -62,7 +68,7 @@ class InfoStruct(C.Structure):
                 ("ms_spmm_w", C.c_double), ("ms_h", C.c_double), ("ms_eig", C.c_double),
                 ("ms_rot", C.c_double), ("ms_resid", C.c_double), ("ms_other", C.c_double),
                 ("filter_bytes", C.c_double), ("filter_ms_kernels", C.c_double),
-                ("n_kernel_launches", C.c_int64)]
+                ("n_kernel_launches", C.c_int64), ("status", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class IterStruct(C.Structure):
@@ -106,6 +112,10 @@ def lib() -> C.CDLL:
         "bchdav_solve_host": (i32, [p, i32, i64, p, p, p, i32, i32, i32, i32, d,
                                     C.POINTER(OptsStruct), p, p, C.POINTER(InfoStruct)]),
         "bchdav_history": (i32, [p, C.POINTER(IterStruct), i32]),
+        "bchdav_solve_batched": (i32, [p, i32, C.POINTER(CSRStruct), p, p, p, p, d,
+                                       C.POINTER(OptsStruct), p, p, C.POINTER(InfoStruct), p]),
+        "bchdav_set_batch_workers": (i32, [p, i32]),
+        "bchdav_launch_count": (i64, []),
         "bchdav_filter": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, i32, d, d, d, i32, p, i32]),
         "bchdav_spmm": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, p, i32]),
         "bchdav_orthonormalize": (i32, [p, i32, p, i32, i32, p, i32, i32, u64, d,
@@ -287,6 +297,36 @@ class Handle:
                                       C.byref(info))
         self._check(st, allow=(0, 1))
         return evals, evecs, self._info(st, info)
+
+    def solve_batched(self, As, k, b, m, act_max, tol, *, precision: int = PREC_MIXED,
+                      seed: int = 0, workers: int = 8, dense_path: int = 0, itmax: int = 0):
+        """Independent solves of many graphs (lists of equal length; act_max entries 0 take the
+        default).  Returns (evals list, evecs list, [SolveInfo], per-graph ms numpy array)."""
+        import numpy as np
+        import torch
+        n = len(As)
+        evals = [torch.zeros(int(k[i]), dtype=torch.float64, device=As[i].rowptr.device)
+                 for i in range(n)]
+        evecs = [torch.zeros((As[i].n, int(k[i])), dtype=torch.float64,
+                             device=As[i].rowptr.device) for i in range(n)]
+        arr = (CSRStruct * n)(*[a.struct() for a in As])
+        i32a = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+        ka, ba, ma, aa = i32a(k), i32a(b), i32a(m), i32a(act_max)
+        pe = np.array([_ptr(t) for t in evals], dtype=np.uint64)
+        pv = np.array([_ptr(t) for t in evecs], dtype=np.uint64)
+        infos = (InfoStruct * n)()
+        ms = np.zeros(n, dtype=np.float32)
+        opts = OptsStruct()
+        opts.precision = precision
+        opts.seed = seed
+        opts.dense_path = dense_path
+        opts.itmax = itmax
+        self._check(self.L.bchdav_set_batch_workers(self.h, workers))
+        st = self.L.bchdav_solve_batched(self.h, n, arr, ka.ctypes.data, ba.ctypes.data,
+                                         ma.ctypes.data, aa.ctypes.data, tol, C.byref(opts),
+                                         pe.ctypes.data, pv.ctypes.data, infos, ms.ctypes.data)
+        self._check(st, allow=(0, 1))
+        return evals, evecs, [self._info(infos[i].status, infos[i]) for i in range(n)], ms
 
     def _info(self, st, info) -> SolveInfo:
         ms = dict(total=info.ms_total, filter=info.ms_filter, orth=info.ms_orth,

@@ -428,33 +428,35 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
 }
 
 cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
-                             int ldy, double* work, int* status) {
+                             int ldy, double* work, int* status, int grid_cap) {
   if (n <= 32) return launch_eigh(st, n, H, ldh, D, Y, ldy, work, status);
   if (n > 1024) return cudaErrorInvalidValue;
   const int np = n + (n & 1);
   const size_t smem = (size_t)(np / 2) * (2 * sizeof(double) + 2 * sizeof(int));
-  static int max_blocks = -1;
-  if (max_blocks < 0) {
+  // one wave of co-resident blocks (thread-safe static initialisation)
+  static const int max_blocks = []() {
     int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel,
-                                                                  kJacThreads, 12 * 1024);
-    if (e != cudaSuccess) return e;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, kJacThreads,
+                                                      12 * 1024) != cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    max_blocks = per_sm * sms;
-  }
+    return std::max(1, per_sm * sms);
+  }();
   // enough threads for the largest round (blocks + vector pairs), at most one wave; the
   // items-per-thread target trades grid-barrier cost against per-round work (tunable with
   // BCHDAV_JACOBI_ITEMS)
-  static int items_per_thread = -1;
-  if (items_per_thread < 0) {
+  static const int items_per_thread = []() {
     const char* env = getenv("BCHDAV_JACOBI_ITEMS");
-    items_per_thread = env ? std::max(1, atoi(env)) : 2;
-  }
+    return env ? std::max(1, atoi(env)) : 2;
+  }();
   long long work_items = (long long)(np / 2) * (np / 2) + (long long)np * (np / 2);
   int grid = ceil_div(work_items, (long long)kJacThreads * items_per_thread);
   if (grid > max_blocks) grid = max_blocks;
   if (grid > 4 * kSMs) grid = 4 * kSMs;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
   JacLayout L = jac_layout(work, n);
   int nn = n, lh = ldh, ly = ldy;

@@ -22,7 +22,11 @@ struct DevBuf {
 
 struct bchdav_handle_s {
   cudaStream_t stream = nullptr;
+  bool owns_stream = false;   // created by the library (batched workers): destroyed with it
   int device = 0;
+  // > 0: block cap of the cooperative kernels (1 for handles whose kernels may run beside
+  // another handle's, so that no cooperative grid can be left partly resident)
+  int coop_grid_cap = 0;
   int sms = bchdav::kSMs;
   std::string err;
   std::vector<DevBuf*> owned;
@@ -37,6 +41,9 @@ struct bchdav_handle_s {
   bchdav::SpmmLong lg;
   const bchdav::SpmmLong* long_rows() const { return lg.n_seg > 0 ? &lg : nullptr; }
   std::vector<bchdav_iter_record> history;
+  // worker handles of bchdav_solve_batched (own streams, cooperative grids capped at one block)
+  std::vector<bchdav_handle_s*> workers;
+  int batch_workers = 8;
   // Pinned staging.  host_pinned belongs to the solve driver; host_aux to the
   // step helpers (filter coefficients, orthonormalisation scalars).  Each helper
   // synchronises the stream before it writes host_aux again, and nothing writes
@@ -101,6 +108,13 @@ struct bchdav_handle_s {
                      &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg};
     lg = bchdav::SpmmLong();
     for (DevBuf* b : all) b->release();
+    for (bchdav_handle_s* w : workers) {
+      cudaStreamSynchronize(w->stream);
+      w->release_all();
+      if (w->owns_stream) cudaStreamDestroy(w->stream);
+      delete w;
+    }
+    workers.clear();
     if (host_pinned) cudaFreeHost(host_pinned);
     host_pinned = nullptr;
     host_pinned_doubles = 0;

@@ -130,10 +130,11 @@ size_t oz_bwork_bytes(int K, int nb);
 // ---------------- orthonormalisation (orth.cu) ----------------
 // Column-by-column classical Gram-Schmidt with two passes inside the block,
 // starting at column j0; stops at the first column found dependent and
-// reports it in *dep (-1 if none).  Cooperative launch.
+// reports it in *dep (-1 if none).  Cooperative launch; grid_cap > 0 bounds its block count
+// (a one-block grid never waits for blocks that are not resident, whatever else runs).
 cudaError_t launch_inblock_gs(cudaStream_t st, int n, double* X, int ldx, int b, int j0,
                               const double* norm0, double tau_dep, double* scratch, int* dep,
-                              double* final_norms);
+                              double* final_norms, int grid_cap = 0);
 size_t inblock_gs_scratch_doubles(int b);
 
 // ---------------- eigensolver (eig.cu) ----------------
@@ -144,7 +145,7 @@ size_t eigh_work_doubles(int n);
 // Same result by parallel cyclic Jacobi over many SMs for n > 32 (launch_eigh below that);
 // work holds eigh_fast_work_doubles(n) doubles.
 cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
-                             int ldy, double* work, int* status);
+                             int ldy, double* work, int* status, int grid_cap = 0);
 size_t eigh_fast_work_doubles(int n);
 
 // ---------------- Laplacian assembly (laplacian.cu) ----------------

@@ -12,6 +12,8 @@
 // so all blocks take the same decisions and results are bitwise reproducible.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -127,22 +129,24 @@ size_t inblock_gs_scratch_doubles(int b) {
 template <int MAXB>
 static cudaError_t launch_gs(cudaStream_t st, int n, double* X, int ldx, int b, int j0,
                              const double* norm0, double tau_dep, double* scratch, int* dep,
-                             double* final_norms) {
-  static int blocks_per_sm = -1;
-  static int sms = -1;
-  if (blocks_per_sm < 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &blocks_per_sm, inblock_gs_kernel<MAXB>, kGsThreads, 0);
-    if (e != cudaSuccess) return e;
-    int dev;
+                             double* final_norms, int grid_cap) {
+  // co-resident blocks, at most 4 per SM (thread-safe static initialisation)
+  static const int wave = []() {
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inblock_gs_kernel<MAXB>,
+                                                      kGsThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (blocks_per_sm > 4) blocks_per_sm = 4;
-  }
-  int grid = blocks_per_sm * sms;
+    return std::max(1, std::min(per_sm, 4) * sms);
+  }();
+  int grid = wave;
   int need = ceil_div(n, kGsThreads);
   if (grid > need) grid = need;
   if (grid > 4 * kSMs) grid = 4 * kSMs;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
   void* args[] = {&n, &X, &ldx, &b, &j0, &norm0, &tau_dep, &scratch, &dep, &final_norms};
   note_launch();
@@ -152,11 +156,12 @@ static cudaError_t launch_gs(cudaStream_t st, int n, double* X, int ldx, int b, 
 
 cudaError_t launch_inblock_gs(cudaStream_t st, int n, double* X, int ldx, int b, int j0,
                               const double* norm0, double tau_dep, double* scratch, int* dep,
-                              double* final_norms) {
+                              double* final_norms, int grid_cap) {
   if (b <= 0 || b > 64) return cudaErrorInvalidValue;
   if (b <= 32)
-    return launch_gs<32>(st, n, X, ldx, b, j0, norm0, tau_dep, scratch, dep, final_norms);
-  return launch_gs<64>(st, n, X, ldx, b, j0, norm0, tau_dep, scratch, dep, final_norms);
+    return launch_gs<32>(st, n, X, ldx, b, j0, norm0, tau_dep, scratch, dep, final_norms,
+                         grid_cap);
+  return launch_gs<64>(st, n, X, ldx, b, j0, norm0, tau_dep, scratch, dep, final_norms, grid_cap);
 }
 
 }  // namespace bchdav

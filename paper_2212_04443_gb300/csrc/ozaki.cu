@@ -303,13 +303,10 @@ static cudaError_t oz_launch_gemm(cudaStream_t st, dim3 grid, int M, int Ma, int
                                   int Np, const int* EB, double* C, int ldc) {
   const size_t smem = sizeof(__nv_bfloat16) * 2 * kOzS * (kOzBM + kOzBN) * kOzRowStride +
                       256 * 8 * sizeof(double);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  // set once per process (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      oz_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return attr;
   oz_gemm_kernel<MODE><<<grid, 256, smem, st>>>(M, Ma, N, Kp, k_split, PA, EA, PB, Np, EB, C, ldc);
   note_launch();
   return cudaGetLastError();

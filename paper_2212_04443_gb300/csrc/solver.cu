@@ -383,7 +383,7 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
     HCUDA(cudaMemcpyAsync(norm0_d, hp, b * sizeof(double), cudaMemcpyHostToDevice, st));
     HCUDA(cudaMemcpyAsync(dep_d, hp + 64, sizeof(int), cudaMemcpyHostToDevice, st));
     HCUDA(launch_inblock_gs(st, n, X, ldx, b, 0, norm0_d, tau_dep, h->small.as<double>(), dep_d,
-                            fin_d));
+                            fin_d, h->coop_grid_cap));
     HCUDA(cudaMemcpyAsync(hp + 64, dep_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     HCUDA(cudaStreamSynchronize(st));
     const int dep = reinterpret_cast<int*>(hp + 64)[0];
@@ -579,7 +579,8 @@ bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t l
   const size_t wd = std::max(eigh_work_doubles(n), eigh_fast_work_doubles(n));
   BCHDAV_TRY(h->ensure(h->eigw, wd * sizeof(double) + 64));
   int* status_d = reinterpret_cast<int*>(h->eigw.as<char>() + wd * sizeof(double));
-  HCUDA(launch_eigh_fast(h->stream, n, H, ld_h, D, Y, ld_y, h->eigw.as<double>(), status_d));
+  HCUDA(launch_eigh_fast(h->stream, n, H, ld_h, D, Y, ld_y, h->eigw.as<double>(), status_d,
+                         h->coop_grid_cap));
   int st = 0;
   HCUDA(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HCUDA(cudaStreamSynchronize(h->stream));
@@ -782,7 +783,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     // Step 9: H Y = Y D (ascending)
     tm_eig.start(st);
     HCUDA(launch_eigh_fast(st, k_act, Hm, act_max, Dd, Ym, act_max, h->eigw.as<double>(),
-                           eig_status));
+                           eig_status, h->coop_grid_cap));
     tm_eig.stop(st);
     HCUDA(cudaMemcpyAsync(hp, Dd, k_act * sizeof(double), cudaMemcpyDeviceToHost, st));
     HCUDA(cudaMemcpyAsync(hp + act_max, eig_status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -132,10 +132,21 @@ def disjoint_union(*graphs: Graph) -> Graph:
 # random families
 # ----------------------------------------------------------------------------
 
+def _sorted_unique(x: np.ndarray) -> np.ndarray:
+    """np.unique of an int64 array (sorted distinct values), by sorting."""
+    x = np.sort(x, kind="stable")
+    if x.shape[0] == 0:
+        return x
+    keep = np.empty(x.shape[0], dtype=bool)
+    keep[0] = True
+    np.not_equal(x[1:], x[:-1], out=keep[1:])
+    return x[keep]
+
+
 def _unique_pairs(u: np.ndarray, v: np.ndarray, n: int) -> np.ndarray:
     lo = np.minimum(u, v).astype(np.int64)
     hi = np.maximum(u, v).astype(np.int64)
-    return np.unique(lo * n + hi)
+    return _sorted_unique(lo * n + hi)
 
 
 def _sample_pairs(g, k, draw, n):
@@ -147,7 +158,7 @@ def _sample_pairs(g, k, draw, n):
         u, v = draw(m)
         ok = u != v
         new = _unique_pairs(u[ok], v[ok], n)
-        keys = np.union1d(keys, new)
+        keys = _sorted_unique(np.concatenate([keys, new]))
         if keys.shape[0] > k:
             keys = g.permutation(keys)[:k]
             keys.sort()
@@ -252,33 +263,59 @@ def knn_gmm_edges(n: int, dim: int = 16, n_comp: int = 50, knn: int = 10, seed: 
     return _as_graph(n, src[keep], dst[keep], f"knn{n}", comp.astype(np.int32))
 
 
+def _rmat_level_tables(probs: np.ndarray, levels: int):
+    """Tables mapping a 16-bit uniform to the i- and j-bits of `levels` consecutive R-MAT
+    levels (bit t = level t of the group).  The outcome probabilities (products of the
+    quadrant probabilities) are quantised to multiples of 2^-16."""
+    p = np.ones(1)
+    for _ in range(levels):
+        p = np.outer(p, probs).ravel()          # outcome index: q_0 * 4^(levels-1) + ... + q_last
+    edges = np.round(np.cumsum(p) * 65536.0).astype(np.int64)
+    edges[-1] = 65536
+    outcome = np.searchsorted(edges, np.arange(65536), side="right")
+    ti = np.zeros(65536, dtype=np.uint32)
+    tj = np.zeros(65536, dtype=np.uint32)
+    for t in range(levels):
+        q = (outcome // 4 ** (levels - 1 - t)) % 4  # quadrant of level t: (i, j) = (q >> 1, q & 1)
+        ti |= ((q >> 1) & 1).astype(np.uint32) << t
+        tj |= (q & 1).astype(np.uint32) << t
+    return ti, tj
+
+
 def rmat_edges(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
                c: float = 0.19, seed: int = 5, chunk: int = 1 << 22) -> Graph:
     """R-MAT sampler (Graph500 parameters by default), no vertex permutation.
 
-    edge_factor * 2^scale directed samples; each picks one quadrant per level
-    with probabilities (a, b, c, 1-a-b-c).
+    edge_factor * 2^scale directed samples; each picks one quadrant per level with
+    probabilities (a, b, c, 1-a-b-c) for (i, j) bits (0,0), (0,1), (1,0), (1,1).  Levels are
+    drawn two at a time from one 16-bit uniform through a table of the 16 joint outcomes (their
+    probabilities quantised to multiples of 2^-16: at most 0.3% relative for the rarest, d*d).
     """
     n = 1 << scale
     m = edge_factor * n
     g = rng(seed)
+    probs = np.array([a, b, c, 1.0 - a - b - c])
+    t2i, t2j = _rmat_level_tables(probs, 2)
+    t1i, t1j = _rmat_level_tables(probs, 1)
+    pairs, odd = divmod(scale, 2)
+    words = (pairs + odd + 3) // 4               # 64-bit draws per edge (four 16-bit uniforms)
     srcs, dsts = [], []
-    ab = a + b
-    c_norm = c / (1.0 - ab)
-    a_norm = a / ab
     for lo in range(0, m, chunk):
         k = min(chunk, m - lo)
-        u = np.zeros(k, dtype=np.int64)
-        v = np.zeros(k, dtype=np.int64)
-        for lvl in range(scale):
-            r1 = g.random(k)
-            r2 = g.random(k)
-            ibit = r1 > ab
-            jbit = np.where(ibit, r2 > c_norm, r2 > a_norm)
-            u |= ibit.astype(np.int64) << lvl
-            v |= jbit.astype(np.int64) << lvl
-        srcs.append(u)
-        dsts.append(v)
+        raw = g.bit_generator.random_raw(k * words).reshape(k, words)
+        u16 = raw.view(np.uint16)                # k x (4 words)
+        u = np.zeros(k, dtype=np.uint32)
+        v = np.zeros(k, dtype=np.uint32)
+        for t in range(pairs):
+            r = u16[:, t]
+            u |= t2i[r] << np.uint32(2 * t)
+            v |= t2j[r] << np.uint32(2 * t)
+        if odd:
+            r = u16[:, pairs]
+            u |= t1i[r] << np.uint32(2 * pairs)
+            v |= t1j[r] << np.uint32(2 * pairs)
+        srcs.append(u.astype(np.int64))
+        dsts.append(v.astype(np.int64))
     src = np.concatenate(srcs)
     dst = np.concatenate(dsts)
     src, dst = reattach_isolated(n, src, dst, g)
