@@ -19,7 +19,9 @@ paper states:
 * ``bchdav``     Algorithm 2, block Chebyshev-Davidson with inner-outer restart
                  and progressive filtering;
 * ``philox``     the Philox4x32-10 counter-based generator (Salmon et al.,
-                 SC 2011) that draws replacement vectors inside the method.
+                 SC 2011) that draws replacement vectors inside the method;
+* ``gnn``        the learned start block (an extension feeding V_init): network,
+                 subspace-alignment loss, its gradient, Adam, Ritz ordering.
 
 Pins (tests/test_oracle_*.py, run with ``-m "not gpu"``): closed-form spectra
 of cycles, paths, hypercubes, complete and complete-bipartite graphs and their
@@ -35,3 +37,4 @@ from .filter import chebyshev_filter, filter_polynomial, chebyshev_T  # noqa: F4
 from .philox import philox4x32_10, uniform_pm_half  # noqa: F401
 from .dgks import dgks_orthonormalize  # noqa: F401
 from .bchdav import bchdav, BchdavResult, default_params, relative_residuals  # noqa: F401
+from . import gnn  # noqa: F401

@@ -58,6 +58,27 @@ def gaussian_block(n: int, cols: int, seed: int = 0) -> np.ndarray:
     return rng(seed).standard_normal((n, cols))
 
 
+def gnn_random_features(n: int, d_r: int, seed: int) -> np.ndarray:
+    """Row-major n x d_r float32 standard normal node features (the network's random inputs)."""
+    return rng(seed).standard_normal((n, d_r)).astype(np.float32)
+
+
+def gnn_init(d_in: int, width: int, k: int, layers: int = 3, seed: int = 0) -> np.ndarray:
+    """Flat float32 initial parameters of the start-block network: every weight matrix
+    (fan_in x fan_out) normal with standard deviation sqrt(1 / fan_in), biases zero, in the
+    order W_1, U_1, b_1, ..., W_L, U_L, b_L, Wo."""
+    g = rng(seed)
+    parts = []
+    p = d_in
+    for _ in range(layers):
+        parts.append(g.standard_normal(p * width) * np.sqrt(1.0 / p))
+        parts.append(g.standard_normal(p * width) * np.sqrt(1.0 / p))
+        parts.append(np.zeros(width))
+        p = width
+    parts.append(g.standard_normal(width * k) * np.sqrt(1.0 / width))
+    return np.concatenate(parts).astype(np.float32)
+
+
 @dataclass
 class Graph:
     """An undirected graph on nodes 0..n-1 given as an edge list."""
