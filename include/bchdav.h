@@ -228,6 +228,41 @@ bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, 
 bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t ld_h, double* D,
                           double* Y, int32_t ld_y);
 
+/* ---- learned start block (an extension feeding Algorithm 2's V_init) ----------
+ * The paper takes an optional block of initial vectors and filters it progressively, best
+ * Rayleigh quotient first (Sec. 3, progressive filtering; Algorithm 2, Step 17).  These calls
+ * run a three-layer message-passing network on Ahat = I - A that proposes such a block:
+ *   X0 = [sqrt(deg)/8, log(1 + deg)/8, R],  S_l = (Ahat H_{l-1}) W_l + H_{l-1} U_l + b_l,
+ *   H_l = relu(S_l), Z = H_3 Wo  (N x k),
+ * trained to align span(Z) with solver eigenvectors U: loss = 1 - tr(G^{-1} P^T P) / k with
+ * G = Z^T Z + rho I, rho = ridge tr(Z^T Z) / k, P = U^T Z.  theta: float32 device vector of
+ * bchdav_gnn_n_params values in the order W_1, U_1, b_1, W_2, U_2, b_2, W_3, U_3, b_3, Wo
+ * (row-major fan_in x fan_out).  R: N x d_r float32 device features.  A needs val_f32.
+ * Shapes: d_r + 2 and width multiples of 4 and at most 64; 1 <= k <= 64. */
+int64_t bchdav_gnn_n_params(int32_t d_r, int32_t width, int32_t k);
+/* Z (N x k float32, device) = network output. */
+bchdav_status bchdav_gnn_forward(bchdav_handle h, const bchdav_csr* A, const float* R,
+                                 int32_t d_r, const float* theta, int32_t width, int32_t k,
+                                 float* Z);
+/* loss (host or device double) and its gradient (device, n_params floats) against U (N x k
+ * float64, ld k, device); Z (may be NULL) receives the output. Synchronises the stream. */
+bchdav_status bchdav_gnn_loss_grad(bchdav_handle h, const bchdav_csr* A, const float* R,
+                                   int32_t d_r, const float* theta, int32_t width, int32_t k,
+                                   const double* U, double ridge, float* grad, double* loss,
+                                   float* Z);
+/* steps x n_graphs Adam updates (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8; one update per
+ * graph, graphs in order) of theta in place; loss_history (host, may be NULL) receives the
+ * loss before each update, row-major steps x n_graphs. */
+bchdav_status bchdav_gnn_train(bchdav_handle h, int32_t n_graphs, const bchdav_csr* As,
+                               const float* const* R, int32_t d_r, const double* const* U,
+                               int32_t width, int32_t k, float* theta, int32_t steps, double lr,
+                               double ridge, double* loss_history);
+/* V0 (N x k float64, ld k, device): orthonormal basis of span(Z) rotated to Ritz vectors,
+ * Rayleigh quotients ascending in ritz (k, device) -- the V_init of bchdav_solve. */
+bchdav_status bchdav_gnn_start_block(bchdav_handle h, const bchdav_csr* A, const float* R,
+                                     int32_t d_r, const float* theta, int32_t width, int32_t k,
+                                     double* V0, double* ritz);
+
 /* ---- allocation-free variant (no counterpart in the paper) --------------- */
 
 /* bchdav_eigh for callers that cannot allocate device memory when they call

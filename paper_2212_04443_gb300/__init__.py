@@ -34,7 +34,8 @@ EXPORTED_SYMBOLS = [
     "bchdav_solve", "bchdav_solve_host", "bchdav_history", "bchdav_filter", "bchdav_spmm",
     "bchdav_orthonormalize", "bchdav_gram", "bchdav_rotate", "bchdav_eigh",
     "bchdav_eigh_noalloc", "bchdav_solve_batched", "bchdav_set_batch_workers",
-    "bchdav_launch_count",
+    "bchdav_launch_count", "bchdav_gnn_n_params", "bchdav_gnn_forward", "bchdav_gnn_loss_grad",
+    "bchdav_gnn_train", "bchdav_gnn_start_block",
 ]
 
 
@@ -116,6 +117,13 @@ def lib() -> C.CDLL:
                                        C.POINTER(OptsStruct), p, p, C.POINTER(InfoStruct), p]),
         "bchdav_set_batch_workers": (i32, [p, i32]),
         "bchdav_launch_count": (i64, []),
+        "bchdav_gnn_n_params": (i64, [i32, i32, i32]),
+        "bchdav_gnn_forward": (i32, [p, C.POINTER(CSRStruct), p, i32, p, i32, i32, p]),
+        "bchdav_gnn_loss_grad": (i32, [p, C.POINTER(CSRStruct), p, i32, p, i32, i32, p, d, p,
+                                       p, p]),
+        "bchdav_gnn_train": (i32, [p, i32, C.POINTER(CSRStruct), p, i32, p, i32, i32, p, i32, d,
+                                   d, p]),
+        "bchdav_gnn_start_block": (i32, [p, C.POINTER(CSRStruct), p, i32, p, i32, i32, p, p]),
         "bchdav_filter": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, i32, d, d, d, i32, p, i32]),
         "bchdav_spmm": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, p, i32]),
         "bchdav_orthonormalize": (i32, [p, i32, p, i32, i32, p, i32, i32, u64, d,
@@ -327,6 +335,60 @@ class Handle:
                                          pe.ctypes.data, pv.ctypes.data, infos, ms.ctypes.data)
         self._check(st, allow=(0, 1))
         return evals, evecs, [self._info(infos[i].status, infos[i]) for i in range(n)], ms
+
+    # ---- learned start block (network feeding V_init)
+    def gnn_n_params(self, d_r: int, width: int, k: int) -> int:
+        return int(self.L.bchdav_gnn_n_params(d_r, width, k))
+
+    @staticmethod
+    def _f32(t):
+        import torch
+        assert t.dtype == torch.float32 and t.is_cuda and t.is_contiguous()
+        return _ptr(t)
+
+    def gnn_forward(self, A: DeviceCSR, R, theta, width: int, k: int):
+        import torch
+        Z = torch.empty((A.n, k), dtype=torch.float32, device=A.rowptr.device)
+        cs = A.struct()
+        self._check(self.L.bchdav_gnn_forward(self.h, C.byref(cs), self._f32(R), R.shape[1],
+                                              self._f32(theta), width, k, _ptr(Z)))
+        return Z
+
+    def gnn_loss_grad(self, A: DeviceCSR, R, theta, U, width: int, k: int, ridge: float = 1e-6):
+        import torch
+        grad = torch.empty_like(theta)
+        Z = torch.empty((A.n, k), dtype=torch.float32, device=A.rowptr.device)
+        loss = C.c_double(0.0)
+        cs = A.struct()
+        assert U.dtype == torch.float64 and U.is_contiguous() and U.shape == (A.n, k)
+        self._check(self.L.bchdav_gnn_loss_grad(self.h, C.byref(cs), self._f32(R), R.shape[1],
+                                                self._f32(theta), width, k, _ptr(U), ridge,
+                                                _ptr(grad), C.addressof(loss), _ptr(Z)))
+        return loss.value, grad, Z
+
+    def gnn_train(self, As, Rs, Us, theta, width: int, k: int, steps: int, lr: float,
+                  ridge: float = 1e-6):
+        """Adam on theta (in place); returns the loss history (steps x graphs)."""
+        import numpy as np
+        n = len(As)
+        arr = (CSRStruct * n)(*[a.struct() for a in As])
+        pr = np.array([self._f32(r) for r in Rs], dtype=np.uint64)
+        pu = np.array([_ptr(u) for u in Us], dtype=np.uint64)
+        hist = np.zeros((steps, n))
+        self._check(self.L.bchdav_gnn_train(self.h, n, arr, pr.ctypes.data, Rs[0].shape[1],
+                                            pu.ctypes.data, width, k, self._f32(theta), steps,
+                                            lr, ridge, hist.ctypes.data))
+        return hist
+
+    def gnn_start_block(self, A: DeviceCSR, R, theta, width: int, k: int):
+        import torch
+        V0 = torch.empty((A.n, k), dtype=torch.float64, device=A.rowptr.device)
+        ritz = torch.empty(k, dtype=torch.float64, device=A.rowptr.device)
+        cs = A.struct()
+        self._check(self.L.bchdav_gnn_start_block(self.h, C.byref(cs), self._f32(R), R.shape[1],
+                                                  self._f32(theta), width, k, _ptr(V0),
+                                                  _ptr(ritz)))
+        return V0, ritz
 
     def _info(self, st, info) -> SolveInfo:
         ms = dict(total=info.ms_total, filter=info.ms_filter, orth=info.ms_orth,

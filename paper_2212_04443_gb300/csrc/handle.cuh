@@ -39,6 +39,7 @@ struct bchdav_handle_s {
   // long-row schedule of the CSR matrix in use (rows over the segment threshold)
   DevBuf lg_cnt, lg_off, lg_tiles, lg_row, lg_pseg;
   bchdav::SpmmLong lg;
+  DevBuf gnn, gnn_opt, gnn_w;   // start-block network: activations, optimiser state, Ritz step
   const bchdav::SpmmLong* long_rows() const { return lg.n_seg > 0 ? &lg : nullptr; }
   std::vector<bchdav_iter_record> history;
   // worker handles of bchdav_solve_batched (own streams, cooperative grids capped at one block)
@@ -105,7 +106,7 @@ struct bchdav_handle_s {
   void release_all() {
     DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
                      &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part,
-                     &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg};
+                     &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w};
     lg = bchdav::SpmmLong();
     for (DevBuf* b : all) b->release();
     for (bchdav_handle_s* w : workers) {
@@ -123,3 +124,7 @@ struct bchdav_handle_s {
     host_aux_doubles = 0;
   }
 };
+
+// Long-row schedule of A (rows with more than kLongRow nonzeros become segments) with segment
+// workspace for products up to width_bytes per row (solver.cu); one host synchronisation.
+bchdav_status prepare_long_rows(bchdav_handle h, const bchdav_csr* A, size_t width_bytes);

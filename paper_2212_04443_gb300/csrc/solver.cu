@@ -60,31 +60,6 @@ struct Timer {
   }
 };
 
-// Long-row schedule of A (rows with more than kLongRow nonzeros become segments), with
-// segment workspace for products up to width_bytes per row.  Rebuilt on every call: it costs
-// one pass over rowptr and one host synchronisation.
-bchdav_status prepare_long_rows(bchdav_handle h, const bchdav_csr* A, size_t width_bytes) {
-  cudaStream_t st = h->stream;
-  const int n = A->n;
-  h->lg = bchdav::SpmmLong();
-  const long long cap = spmm_long_seg_cap(A->nnz);
-  BCHDAV_TRY(h->ensure(h->lg_cnt, (size_t)n * sizeof(int)));
-  BCHDAV_TRY(h->ensure(h->lg_off, (size_t)(n + 1) * sizeof(long long)));
-  BCHDAV_TRY(h->ensure(h->lg_tiles, (size_t)scan_tile_count(n) * sizeof(long long) + 64));
-  BCHDAV_TRY(h->ensure(h->lg_row, (size_t)cap * sizeof(int)));
-  long long total = 0, n_seg = 0;
-  HCUDA(build_spmm_long(st, n, A->rowptr, h->lg_cnt.as<int>(), h->lg_off.as<long long>(),
-                        h->lg_tiles.as<long long>(), h->lg_row.as<int>(), cap, &total, &n_seg));
-  if (n_seg > 0) {
-    BCHDAV_TRY(h->ensure(h->lg_pseg, (size_t)n_seg * width_bytes));
-    h->lg.n_seg = n_seg;
-    h->lg.seg_off = h->lg_off.as<long long>();
-    h->lg.seg_row = h->lg_row.as<int>();
-    h->lg.pseg = h->lg_pseg.p;
-  }
-  return BCHDAV_OK;
-}
-
 // ---------------- Algorithm 3 ----------------
 // Y = p_m(A) X.  prec MIXED: recurrence in float32 (val32 required).
 bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val32, const double* X,
@@ -409,6 +384,30 @@ double median_of(std::vector<double> v) {
 }
 
 }  // namespace
+
+// Long-row schedule (declared in handle.cuh).  Rebuilt on every call: it costs one pass over
+// rowptr and one host synchronisation.
+bchdav_status prepare_long_rows(bchdav_handle h, const bchdav_csr* A, size_t width_bytes) {
+  cudaStream_t st = h->stream;
+  const int n = A->n;
+  h->lg = bchdav::SpmmLong();
+  const long long cap = spmm_long_seg_cap(A->nnz);
+  BCHDAV_TRY(h->ensure(h->lg_cnt, (size_t)n * sizeof(int)));
+  BCHDAV_TRY(h->ensure(h->lg_off, (size_t)(n + 1) * sizeof(long long)));
+  BCHDAV_TRY(h->ensure(h->lg_tiles, (size_t)scan_tile_count(n) * sizeof(long long) + 64));
+  BCHDAV_TRY(h->ensure(h->lg_row, (size_t)cap * sizeof(int)));
+  long long total = 0, n_seg = 0;
+  HCUDA(build_spmm_long(st, n, A->rowptr, h->lg_cnt.as<int>(), h->lg_off.as<long long>(),
+                        h->lg_tiles.as<long long>(), h->lg_row.as<int>(), cap, &total, &n_seg));
+  if (n_seg > 0) {
+    BCHDAV_TRY(h->ensure(h->lg_pseg, (size_t)n_seg * width_bytes));
+    h->lg.n_seg = n_seg;
+    h->lg.seg_off = h->lg_off.as<long long>();
+    h->lg.seg_row = h->lg_row.as<int>();
+    h->lg.pseg = h->lg_pseg.p;
+  }
+  return BCHDAV_OK;
+}
 
 namespace bchdav {
 // Message returned by bchdav_last_error(NULL) for entry points without a handle.
