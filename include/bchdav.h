@@ -173,6 +173,9 @@ bchdav_status bchdav_solve_batched(bchdav_handle h, int32_t n_graphs, const bchd
                                    double* const* evals, double* const* evecs,
                                    bchdav_info* infos, float* per_graph_ms);
 
+/* Free every device and pinned buffer the handle holds (the next call allocates again). */
+bchdav_status bchdav_release_workspace(bchdav_handle h);
+
 /* Kernels this library has launched in the process so far (all handles). */
 int64_t bchdav_launch_count(void);
 

@@ -122,7 +122,9 @@ def loss_and_grad(A, X0, theta, U, width, k, ridge=1e-6, layers: int = N_LAYERS)
 
 
 def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One Adam update (Kingma and Ba, 2015) with bias correction; t counts from 1."""
+    """One Adam update (Kingma and Ba, 2015) with bias correction; t counts from 1.
+    Non-finite gradient components count as zero."""
+    grad = np.where(np.isfinite(grad), grad, 0.0)
     m = beta1 * m + (1 - beta1) * grad
     v = beta2 * v + (1 - beta2) * grad * grad
     mh = m / (1 - beta1 ** t)

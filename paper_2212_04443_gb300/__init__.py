@@ -35,7 +35,7 @@ EXPORTED_SYMBOLS = [
     "bchdav_orthonormalize", "bchdav_gram", "bchdav_rotate", "bchdav_eigh",
     "bchdav_eigh_noalloc", "bchdav_solve_batched", "bchdav_set_batch_workers",
     "bchdav_launch_count", "bchdav_gnn_n_params", "bchdav_gnn_forward", "bchdav_gnn_loss_grad",
-    "bchdav_gnn_train", "bchdav_gnn_start_block",
+    "bchdav_gnn_train", "bchdav_gnn_start_block", "bchdav_release_workspace",
 ]
 
 
@@ -117,6 +117,7 @@ def lib() -> C.CDLL:
                                        C.POINTER(OptsStruct), p, p, C.POINTER(InfoStruct), p]),
         "bchdav_set_batch_workers": (i32, [p, i32]),
         "bchdav_launch_count": (i64, []),
+        "bchdav_release_workspace": (i32, [p]),
         "bchdav_gnn_n_params": (i64, [i32, i32, i32]),
         "bchdav_gnn_forward": (i32, [p, C.POINTER(CSRStruct), p, i32, p, i32, i32, p]),
         "bchdav_gnn_loss_grad": (i32, [p, C.POINTER(CSRStruct), p, i32, p, i32, i32, p, d, p,
@@ -336,6 +337,10 @@ class Handle:
         self._check(st, allow=(0, 1))
         return evals, evecs, [self._info(infos[i].status, infos[i]) for i in range(n)], ms
 
+    def release_workspace(self):
+        """Free the handle's device workspace (reallocated by the next call)."""
+        self._check(self.L.bchdav_release_workspace(self.h))
+
     # ---- learned start block (network feeding V_init)
     def gnn_n_params(self, d_r: int, width: int, k: int) -> int:
         return int(self.L.bchdav_gnn_n_params(d_r, width, k))
@@ -367,7 +372,7 @@ class Handle:
         return loss.value, grad, Z
 
     def gnn_train(self, As, Rs, Us, theta, width: int, k: int, steps: int, lr: float,
-                  ridge: float = 1e-6):
+                  ridge: float = 1e-4):
         """Adam on theta (in place); returns the loss history (steps x graphs)."""
         import numpy as np
         n = len(As)

@@ -46,6 +46,13 @@ bchdav_status make_worker(bchdav_handle parent, bchdav_handle* out) {
 
 extern "C" {
 
+bchdav_status bchdav_release_workspace(bchdav_handle h) {
+  if (!h) return BCHDAV_ERR_ARG;
+  HCUDA(cudaStreamSynchronize(h->stream));
+  h->release_all();
+  return BCHDAV_OK;
+}
+
 int64_t bchdav_launch_count(void) {
   return (int64_t)__atomic_load_n(&bchdav::g_launches, __ATOMIC_RELAXED);
 }

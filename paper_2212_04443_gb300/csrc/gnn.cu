@@ -278,7 +278,7 @@ __global__ void gnn_adam_kernel(int n, float* __restrict__ theta, const float* _
                                 float* __restrict__ m, float* __restrict__ v, float lr, float b1,
                                 float b2, float c1, float c2, float eps) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float gi = g[i];
+    const float gi = isfinite(g[i]) ? g[i] : 0.f;   // a non-finite component is skipped
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -584,6 +584,9 @@ bchdav_status bchdav_gnn_start_block(bchdav_handle h, const bchdav_csr* A, const
   BCHDAV_TRY(bchdav_eigh(h, k, Hq, k, ritz, Y, k));
   BCHDAV_TRY(bchdav_rotate(h, n, V0, k, k, Y, k, k, 0));
   HCUDA(cudaStreamSynchronize(st));
+  // one-shot N-sized buffers: give the memory back to the solve that follows
+  h->gnn.release();
+  h->gnn_w.release();
   return BCHDAV_OK;
 }
 

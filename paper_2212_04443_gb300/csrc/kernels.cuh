@@ -38,14 +38,13 @@ cudaError_t launch_spmm_axpby(cudaStream_t st, int n, const int* rowptr, const i
                               const T* R = nullptr, int ldr = 0, const T* delta = nullptr,
                               const SpmmLong* lg = nullptr);
 
-// Residual of Step 12: for column j, r_j = (A V)_j - d_j V_j; writes per-CTA
-// partial sums of r_j^2 and v_j^2 to partial[cta * 2b + {j, b + j}] and
-// returns the CTA count in *n_parts.  The vectors r_j are stored in Rout
-// (ld ldr) when it is not NULL.
+// Residual of Step 12: R = A V - V diag(d) into Rout (n x b, ldr >= b; required), then
+// per-CTA partial sums of r_j^2 and v_j^2 in partial[cta * 2b + {j, b + j}]; the CTA count
+// is returned in *n_parts.  negd: b doubles of device scratch.
 cudaError_t launch_spmm_resid(cudaStream_t st, int n, const int* rowptr, const int* colidx,
                               const double* val, const double* V, int ldv, int b,
-                              const double* d, double* partial, int* n_parts,
-                              double* Rout = nullptr, int ldr = 0, const SpmmLong* lg = nullptr);
+                              const double* d, double* partial, int* n_parts, double* Rout,
+                              int ldr, double* negd, const SpmmLong* lg = nullptr);
 int spmm_resid_max_parts(int n, int b);
 
 // ---------------- dense family (dense.cu) ----------------

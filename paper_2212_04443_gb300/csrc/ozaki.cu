@@ -40,7 +40,11 @@ constexpr int kOzMaxK = 448;     // bound used for the one-shot products (exact 
 constexpr int kOzBM = 64;        // CTA tile rows
 constexpr int kOzBN = 32;        // CTA tile columns
 constexpr int kOzBK = 16;        // k step
-constexpr int kOzRowStride = 24; // smem row stride (bf16) of a 16-wide k tile: conflict-free
+constexpr int kOzStages = 3;     // cp.async pipeline depth
+// shared-memory tile rows are 16 bf16 (two 16-byte halves); half h of row r is stored at
+// position h ^ ((r >> 2) & 1), so that the eight rows a fragment load touches fall on
+// distinct banks without padding
+__device__ __forceinline__ int oz_sw(int r, int half) { return r * 16 + ((half ^ ((r >> 2) & 1)) << 3); }
 constexpr int kOzChunk = 1024;   // rows per exponent chunk of a Gram operand (64 k steps of 16)
 
 // --- digit extraction ------------------------------------------------------
@@ -172,11 +176,11 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
                                                       const int* __restrict__ EB,
                                                       double* __restrict__ C, int ldc) {
   extern __shared__ __align__(16) unsigned char oz_smem[];
-  // sA[buf][s][row * kOzRowStride + k], sB likewise, then 8 float64 per thread (90 KB of
-  // dynamic shared memory: two CTAs per SM)
-  auto sA = reinterpret_cast<__nv_bfloat16(*)[kOzS][kOzBM * kOzRowStride]>(oz_smem);
-  auto sB = reinterpret_cast<__nv_bfloat16(*)[kOzS][kOzBN * kOzRowStride]>(
-      oz_smem + sizeof(__nv_bfloat16) * 2 * kOzS * kOzBM * kOzRowStride);
+  // sA[stage][s][swizzled row-major 64 x 16], sB likewise (32 x 16), then 8 float64 per
+  // thread (88 KB of dynamic shared memory: two CTAs per SM)
+  auto sA = reinterpret_cast<__nv_bfloat16(*)[kOzS][kOzBM * 16]>(oz_smem);
+  auto sB = reinterpret_cast<__nv_bfloat16(*)[kOzS][kOzBN * 16]>(
+      oz_smem + sizeof(__nv_bfloat16) * kOzStages * kOzS * kOzBM * 16);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int wm = warp & 3, wn = warp >> 2;
   const int r0 = blockIdx.x * kOzBM, c0 = blockIdx.y * kOzBN;
@@ -190,14 +194,14 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
     for (int q = t; q < kOzS * kOzBM * 2; q += 256) {
       const int s = q / (kOzBM * 2), rem = q - s * kOzBM * 2, row = rem >> 1, half = rem & 1;
       const int gr = r0 + row;
-      __nv_bfloat16* dst = &sA[buf][s][row * kOzRowStride + half * 8];
+      __nv_bfloat16* dst = &sA[buf][s][oz_sw(row, half)];
       if (gr < M) cp_async16(dst, PA + s * planeA + (size_t)gr * Kp + k0 + half * 8);
       else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
     for (int q = t; q < kOzS * kOzBN * 2; q += 256) {
       const int s = q / (kOzBN * 2), rem = q - s * kOzBN * 2, row = rem >> 1, half = rem & 1;
       const int gc = c0 + row;
-      __nv_bfloat16* dst = &sB[buf][s][row * kOzRowStride + half * 8];
+      __nv_bfloat16* dst = &sB[buf][s][oz_sw(row, half)];
       if (gc < Np) cp_async16(dst, PB + s * planeB + (size_t)gc * Kp + k0 + half * 8);
       else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
   float acc[kOzS][2][4];
   // float64 partial sums live in shared memory (touched only at flushes), 8 per thread
   double* dacc = reinterpret_cast<double*>(
-      oz_smem + sizeof(__nv_bfloat16) * 2 * kOzS * (kOzBM + kOzBN) * kOzRowStride) + t * 8;
+      oz_smem + sizeof(__nv_bfloat16) * kOzStages * kOzS * (kOzBM + kOzBN) * 16) + t * 8;
 #pragma unroll
   for (int e = 0; e < 8; ++e) dacc[e] = 0.0;
   auto zero_acc = [&]() {
@@ -241,29 +245,33 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
   };
   zero_acc();
 
-  if (kt0 < kt1) load_stage(0, kt0 * kOzBK);
+  const int nst = kt1 - kt0;
+  if (nst > 0) load_stage(0, kt0 * kOzBK);
+  if (nst > 1) load_stage(1, (kt0 + 1) * kOzBK);
   for (int kt = kt0; kt < kt1; ++kt) {
-    const int buf = (kt - kt0) & 1;
-    cp_async_wait0();
+    const int i = kt - kt0, buf = i % kOzStages;
+    // stage i has landed once at most one later group is pending
+    if (i + 1 < nst) cp_async_wait<1>();
+    else cp_async_wait0();
     __syncthreads();
-    if (kt + 1 < kt1) load_stage(buf ^ 1, (kt + 1) * kOzBK);
+    if (i + 2 < nst) load_stage((i + 2) % kOzStages, (kt + 2) * kOzBK);
     uint32_t bf[kOzS][2][2];
 #pragma unroll
     for (int s = 0; s < kOzS; ++s)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const __nv_bfloat16* base = &sB[buf][s][(wn * 16 + j * 8 + g) * kOzRowStride];
-        bf[s][j][0] = *reinterpret_cast<const uint32_t*>(base + tig * 2);
-        bf[s][j][1] = *reinterpret_cast<const uint32_t*>(base + tig * 2 + 8);
+        const int r = wn * 16 + j * 8 + g;
+        bf[s][j][0] = *reinterpret_cast<const uint32_t*>(&sB[buf][s][oz_sw(r, 0) + tig * 2]);
+        bf[s][j][1] = *reinterpret_cast<const uint32_t*>(&sB[buf][s][oz_sw(r, 1) + tig * 2]);
       }
 #pragma unroll
     for (int s = 0; s < kOzS; ++s) {
       uint32_t af[4];
-      const __nv_bfloat16* base = &sA[buf][s][(wm * 16 + g) * kOzRowStride];
-      af[0] = *reinterpret_cast<const uint32_t*>(base + tig * 2);
-      af[1] = *reinterpret_cast<const uint32_t*>(base + 8 * kOzRowStride + tig * 2);
-      af[2] = *reinterpret_cast<const uint32_t*>(base + tig * 2 + 8);
-      af[3] = *reinterpret_cast<const uint32_t*>(base + 8 * kOzRowStride + tig * 2 + 8);
+      const int r = wm * 16 + g;
+      af[0] = *reinterpret_cast<const uint32_t*>(&sA[buf][s][oz_sw(r, 0) + tig * 2]);
+      af[1] = *reinterpret_cast<const uint32_t*>(&sA[buf][s][oz_sw(r + 8, 0) + tig * 2]);
+      af[2] = *reinterpret_cast<const uint32_t*>(&sA[buf][s][oz_sw(r, 1) + tig * 2]);
+      af[3] = *reinterpret_cast<const uint32_t*>(&sA[buf][s][oz_sw(r + 8, 1) + tig * 2]);
 #pragma unroll
       for (int tt = 0; tt < kOzS; ++tt) {
         if (s + tt < kOzS) {   // levels s + tt + 2 <= 9
@@ -301,7 +309,7 @@ template <int MODE>
 static cudaError_t oz_launch_gemm(cudaStream_t st, dim3 grid, int M, int Ma, int N, int Kp, int k_split,
                                   const __nv_bfloat16* PA, const int* EA, const __nv_bfloat16* PB,
                                   int Np, const int* EB, double* C, int ldc) {
-  const size_t smem = sizeof(__nv_bfloat16) * 2 * kOzS * (kOzBM + kOzBN) * kOzRowStride +
+  const size_t smem = sizeof(__nv_bfloat16) * kOzStages * kOzS * (kOzBM + kOzBN) * 16 +
                       256 * 8 * sizeof(double);
   // set once per process (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(

@@ -637,7 +637,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   BCHDAV_TRY(h->ensure(h->R, (size_t)N * ldb * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->H, (size_t)act_max * act_max * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->Y, (size_t)act_max * act_max * sizeof(double)));
-  BCHDAV_TRY(h->ensure(h->D, (size_t)(act_max + 256 + ncols + 64) * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->D, (size_t)(act_max + 256 + ncols + 64 + 128) * sizeof(double)));
   const size_t eig_wd = std::max(eigh_work_doubles(act_max), eigh_fast_work_doubles(act_max));
   BCHDAV_TRY(h->ensure(h->eigw, eig_wd * sizeof(double) + 64));
   const int chunks = gemm_tn_chunks(N);
@@ -676,6 +676,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   double* Dd = h->D.as<double>();            // act_max Ritz values
   double* dsel = Dd + act_max;               // device staging for small vectors (256)
   int* perm_d = reinterpret_cast<int*>(dsel + 256);   // ncols column indices
+  double* negd = Dd + act_max + 256 + ncols + 64;      // 128: -d of the residual epilogue
   int* eig_status = reinterpret_cast<int*>(h->eigw.as<char>() + eig_wd * sizeof(double));
   double* hp = h->host_pinned;
   h->history.clear();
@@ -723,7 +724,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   std::vector<int> mix_src(b, -1);
   std::vector<double> mix_theta(b, NAN);
   const int ldr = round_up(2 * b, 2);
-  if (prec == BCHDAV_PREC_MIXED) BCHDAV_TRY(h->ensure(h->Rres, (size_t)N * ldr * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->Rres, (size_t)N * ldr * sizeof(double)));   // Step 12 residual block
 
   while (it < itmax) {
     ++it;
@@ -815,9 +816,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     tm_res.start(st);
     int nparts = 0;
     HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c, ldv, nres, Dd,
-                            h->part.as<double>(), &nparts,
-                            prec == BCHDAV_PREC_MIXED ? h->Rres.as<double>() : nullptr, ldr,
-                            h->long_rows()));
+                            h->part.as<double>(), &nparts, h->Rres.as<double>(), ldr,
+                            negd, h->long_rows()));
     HCUDA(launch_reduce_partials(st, h->part.as<double>(), nparts, 2 * nres, dsel, 1.0));
     HCUDA(cudaMemcpyAsync(hp + act_max + 1, dsel, 2 * nres * sizeof(double), cudaMemcpyDeviceToHost,
                           st));
@@ -950,11 +950,12 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     HCUDA(cudaMemcpyAsync(evals, ev, n_out * sizeof(double), cudaMemcpyHostToDevice, st));
     HCUDA(launch_gather_cols(st, N, n_out, V, ldv, perm_d, evecs, k));
     // final check: fresh float64 residuals of the returned pairs
-    for (int c0 = 0; c0 < n_out; c0 += 64) {
-      int w = std::min(64, n_out - c0);
+    for (int c0 = 0; c0 < n_out; c0 += std::min(64, ldr)) {
+      int w = std::min(std::min(64, ldr), n_out - c0);
       int np = 0;
       HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, evecs + c0, k, w, evals + c0,
-                              h->part.as<double>(), &np, nullptr, 0, h->long_rows()));
+                              h->part.as<double>(), &np, h->Rres.as<double>(), ldr, negd,
+                              h->long_rows()));
       HCUDA(launch_reduce_partials(st, h->part.as<double>(), np, 2 * w, dsel, 1.0));
       HCUDA(cudaMemcpyAsync(hp + 1024 - 128, dsel, 2 * w * sizeof(double), cudaMemcpyDeviceToHost, st));
       HCUDA(cudaStreamSynchronize(st));

@@ -322,41 +322,32 @@ template cudaError_t launch_spmm_axpby<float>(cudaStream_t, int, const int*, con
                                               int, const float*, const SpmmLong*);
 
 // ---------------- residual norms (Step 12) ----------------
+// R = A V - V diag(d) through the row kernel (all rows in flight at once; the product's
+// epilogue subtracts d_j v_j), then one streaming pass for the per-CTA partial sums of r_j^2
+// and v_j^2 (fixed order: deterministic).
 constexpr int kResidThreads = 256;
 
-__global__ void __launch_bounds__(kResidThreads) spmm_resid_kernel(
-    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-    const double* __restrict__ val, const double* __restrict__ V, int ldv, int b,
-    const double* __restrict__ d, double* __restrict__ partial, double* __restrict__ Rout,
-    int ldr, const long long* __restrict__ seg_off, const double* __restrict__ pseg) {
-  // one thread per (row, column); block covers rows_per_block rows of all b columns
-  extern __shared__ double sh[];
+__global__ void negate_kernel(int b, const double* __restrict__ d, double* __restrict__ out) {
+  for (int j = threadIdx.x; j < b; j += blockDim.x) out[j] = -d[j];
+}
+
+__global__ void __launch_bounds__(kResidThreads) resid_norms_kernel(
+    int n, const double* __restrict__ R, int ldr, const double* __restrict__ V, int ldv, int b,
+    double* __restrict__ partial) {
+  __shared__ double s_r[kResidThreads];
+  __shared__ double s_v[kResidThreads];
   const int rpb = kResidThreads / b;
   const int t = threadIdx.x;
-  const int rl = t / b;
-  const int c = t - rl * b;
+  const int rl = t / b, c = t - rl * b;
   double r2 = 0.0, v2 = 0.0;
-  if (rl < rpb) {
+  if (rl < rpb)
     for (int row = blockIdx.x * rpb + rl; row < n; row += gridDim.x * rpb) {
-      double acc[1] = {0.0};
-      const int p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
-      if (seg_off != nullptr && p1 - p0 > kLongRow) {
-        for (long long s = seg_off[row]; s < seg_off[row + 1]; ++s) acc[0] += pseg[s * b + c];
-      } else {
-        row_product<double, 1>(colidx, val, V, ldv, c, p0, p1, acc);
-      }
-      double v = __ldg(V + (size_t)row * ldv + c);
-      double r = fma(-__ldg(d + c), v, acc[0]);
-      if (Rout != nullptr) Rout[(size_t)row * ldr + c] = r;
+      const double r = R[(size_t)row * ldr + c], v = V[(size_t)row * ldv + c];
       r2 = fma(r, r, r2);
       v2 = fma(v, v, v2);
     }
-  }
-  // deterministic reduction over the rpb row slots of each column
-  double* s_r = sh;
-  double* s_v = sh + kResidThreads;
-  s_r[t] = (rl < rpb) ? r2 : 0.0;
-  s_v[t] = (rl < rpb) ? v2 : 0.0;
+  s_r[t] = rl < rpb ? r2 : 0.0;
+  s_v[t] = rl < rpb ? v2 : 0.0;
   __syncthreads();
   if (t < b) {
     double ar = 0.0, av = 0.0;
@@ -378,27 +369,17 @@ int spmm_resid_max_parts(int n, int b) {
 cudaError_t launch_spmm_resid(cudaStream_t st, int n, const int* rowptr, const int* colidx,
                               const double* val, const double* V, int ldv, int b,
                               const double* d, double* partial, int* n_parts, double* Rout,
-                              int ldr, const SpmmLong* lg) {
-  if (b > kResidThreads || b <= 0) return cudaErrorInvalidValue;
-  int grid = spmm_resid_max_parts(n, b);
+                              int ldr, double* negd, const SpmmLong* lg) {
+  if (b > kResidThreads || b <= 0 || Rout == nullptr || negd == nullptr || ldr < b)
+    return cudaErrorInvalidValue;
+  negate_kernel<<<1, 64, 0, st>>>(b, d, negd); note_launch();
+  cudaError_t e = launch_spmm_axpby<double>(st, n, rowptr, colidx, val, V, ldv, b, Rout, ldr,
+                                            nullptr, 0, 1.0, 0.0, 0.0, V, ldv, negd, lg);
+  if (e != cudaSuccess) return e;
+  const int grid = spmm_resid_max_parts(n, b);
   *n_parts = grid;
-  const long long* seg_off = nullptr;
-  const double* pseg = nullptr;
-  if (lg != nullptr && lg->n_seg > 0) {
-    if (lg->n_seg > 0x7fffffffLL) return cudaErrorInvalidValue;
-    double* ps = static_cast<double*>(lg->pseg);
-    // segment products of A V in column chunks of at most 32 (one lane per column)
-    for (int c0 = 0; c0 < b; c0 += 32) {
-      const int w = std::min(32, b - c0);
-      spmm_long_seg_kernel<double, 1><<<(unsigned)lg->n_seg, 256, 0, st>>>(
-          rowptr, colidx, val, V + c0, ldv, w, w, lg->seg_off, lg->seg_row, ps + c0, b);
-      note_launch();
-    }
-    seg_off = lg->seg_off;
-    pseg = ps;
-  }
-  spmm_resid_kernel<<<grid, kResidThreads, 2 * kResidThreads * sizeof(double), st>>>(
-      n, rowptr, colidx, val, V, ldv, b, d, partial, Rout, ldr, seg_off, pseg); note_launch();
+  resid_norms_kernel<<<grid, kResidThreads, 0, st>>>(n, Rout, ldr, V, ldv, b, partial);
+  note_launch();
   return cudaGetLastError();
 }
 

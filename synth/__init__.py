@@ -362,18 +362,22 @@ def workload(name: str) -> dict:
     if base == "sbm10k":
         n = int(size) if size else 10000
         gr = sbm_edges(n, 10, p_in=1e-3 * 10000 / n, p_out=2e-5 * 10000 / n, seed=1)
-        return dict(graph=gr, k=10, b=5, m=11, act_max=30, tol=tol, v0_seed=0)
+        return dict(graph=gr, k=10, b=5, m=11, act_max=30, tol=tol, v0_seed=0,
+                    desc=f"SBM N={n} c=10 p_in=1e-3 p_out=2e-5")
     if base == "sbm1m":
         n = int(size) if size else 1000000
         c = 100 if n >= 100000 else max(4, n // 10000)
         gr = sbm_edges(n, c, d_in=16.0, d_out=2.0, seed=2)
-        return dict(graph=gr, k=c, b=20, m=15, act_max=300, tol=tol, v0_seed=0)
+        return dict(graph=gr, k=c, b=20, m=15, act_max=300, tol=tol, v0_seed=0,
+                    desc=f"SBM N={n} c={c} d_in=16 d_out=2")
     if base == "knn2m":
         n = int(size) if size else 2000000
         gr = knn_gmm_edges(n, seed=3)
-        return dict(graph=gr, k=50, b=10, m=13, act_max=150, tol=tol, v0_seed=0)
+        return dict(graph=gr, k=50, b=10, m=13, act_max=150, tol=tol, v0_seed=0,
+                    desc=f"kNN graph of {n} points, 16-D 50-component Gaussian mixture, 10-NN")
     if base == "rmat24":
         scale = int(size) if size else 24
         gr = rmat_edges(scale, seed=5)
-        return dict(graph=gr, k=64, b=16, m=15, act_max=192, tol=tol, v0_seed=0)
+        return dict(graph=gr, k=64, b=16, m=15, act_max=192, tol=tol, v0_seed=0,
+                    desc=f"R-MAT scale {scale} edge factor 16 (0.57, 0.19, 0.19, 0.05)")
     raise KeyError(name)

@@ -81,7 +81,7 @@ def test_training_follows_oracle_adam(H):
         Us.append(U); Uds.append(torch.from_numpy(U).cuda())
     theta0 = synth.gnn_init(D_R + 2, WIDTH, k, seed=80)
     Td = torch.from_numpy(theta0.copy()).cuda()
-    hist = H.gnn_train(As, Rds, Uds, Td, WIDTH, k, steps, lr)
+    hist = H.gnn_train(As, Rds, Uds, Td, WIDTH, k, steps, lr, ridge=1e-4)
     th = theta0.astype(np.float64)
     m = np.zeros_like(th)
     v = np.zeros_like(th)
@@ -89,7 +89,7 @@ def test_training_follows_oracle_adam(H):
     for s in range(steps):
         for i in range(2):
             loss, grad, _ = gnn.loss_and_grad(Ls[i].scipy(), gnn.features(Ls[i], Rs[i]), th,
-                                              Us[i], WIDTH, k)
+                                              Us[i], WIDTH, k, ridge=1e-4)
             assert abs(hist[s, i] - loss) <= 2e-3, (s, i, hist[s, i], loss)
             t += 1
             th, m, v = gnn.adam_step(th, grad, m, v, t, lr)
