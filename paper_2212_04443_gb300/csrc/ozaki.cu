@@ -151,6 +151,15 @@ __device__ __forceinline__ void oz_mma(float (&d)[4], const uint32_t (&a)[4], co
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// four 8x8 bf16 matrices from shared memory, one row address per lane (lanes 8i..8i+7 for
+// matrix i); lane t receives row t/4, columns 2(t%4), 2(t%4)+1 of each: the mma fragment layout
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* smem_row) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
@@ -255,23 +264,24 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
     else cp_async_wait0();
     __syncthreads();
     if (i + 2 < nst) load_stage((i + 2) % kOzStages, (kt + 2) * kOzBK);
+    // fragments by ldmatrix: lane l addresses row (l & 7) of matrix l >> 3
+    const int mi = lane >> 3, rr = lane & 7;
     uint32_t bf[kOzS][2][2];
 #pragma unroll
-    for (int s = 0; s < kOzS; ++s)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int r = wn * 16 + j * 8 + g;
-        bf[s][j][0] = *reinterpret_cast<const uint32_t*>(&sB[buf][s][oz_sw(r, 0) + tig * 2]);
-        bf[s][j][1] = *reinterpret_cast<const uint32_t*>(&sB[buf][s][oz_sw(r, 1) + tig * 2]);
-      }
+    for (int s = 0; s < kOzS; ++s) {
+      // matrices: (n-tile 0, k half 0), (0, 1), (1, 0), (1, 1)
+      uint32_t q[4];
+      ldsm_x4(q, &sB[buf][s][oz_sw(wn * 16 + (mi >> 1) * 8 + rr, mi & 1)]);
+      bf[s][0][0] = q[0];
+      bf[s][0][1] = q[1];
+      bf[s][1][0] = q[2];
+      bf[s][1][1] = q[3];
+    }
 #pragma unroll
     for (int s = 0; s < kOzS; ++s) {
+      // matrices: (rows 0-7, k half 0), (rows 8-15, 0), (rows 0-7, 1), (rows 8-15, 1)
       uint32_t af[4];
-      const int r = wm * 16 + g;
-      af[0] = *reinterpret_cast<const uint32_t*>(&sA[buf][s][oz_sw(r, 0) + tig * 2]);
-      af[1] = *reinterpret_cast<const uint32_t*>(&sA[buf][s][oz_sw(r + 8, 0) + tig * 2]);
-      af[2] = *reinterpret_cast<const uint32_t*>(&sA[buf][s][oz_sw(r, 1) + tig * 2]);
-      af[3] = *reinterpret_cast<const uint32_t*>(&sA[buf][s][oz_sw(r + 8, 1) + tig * 2]);
+      ldsm_x4(af, &sA[buf][s][oz_sw(wm * 16 + (mi & 1) * 8 + rr, mi >> 1)]);
 #pragma unroll
       for (int tt = 0; tt < kOzS; ++tt) {
         if (s + tt < kOzS) {   // levels s + tt + 2 <= 9
