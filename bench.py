@@ -140,9 +140,18 @@ def rotation_flops(hist, n):
     return sum(2.0 * n * h.k_old * h.k_act for h in hist)
 
 
-# Each float64-accurate product runs as 36 bf16 x bf16 -> f32 tensor-core products of
-# digit slices (8 slices, pairs s + t <= 9; see csrc/ozaki.cu).
-SLICE_PAIRS = 36
+# A slice product with S digit slices runs S (S + 1) / 2 bf16 x bf16 -> f32 tensor-core
+# products (pairs s + t < S; see csrc/ozaki.cu): 36 for S = 8 (float64-accurate), 21 for S = 6
+# (the mixed path's Step-11 rotation).
+def slice_pairs(S):
+    return S * (S + 1) // 2
+
+
+# pairs per float64-equivalent flop of each component, by path
+PAIRS = {
+    "f64": {"rotation": 36, "rayleigh_quotient": 36, "orthonormalisation": 36},
+    "mixed": {"rotation": 21, "rayleigh_quotient": 36, "orthonormalisation": 36},
+}
 
 
 def orth_flops(hist, n, b):
@@ -234,10 +243,12 @@ def run_ours(args):
             c["achieved"] = c["work"] / s / 1e9 if s > 0 else 0.0
             c["peak"] = hbm_peak
         elif tensor_path:
-            # float64-accurate products executed as SLICE_PAIRS bf16 tensor-core products
+            # products executed as slice-pair bf16 tensor-core products
+            pairs = PAIRS["mixed" if prec == P.PREC_MIXED else "f64"][name]
             c["bound"] = "tensor"
+            c["slice_pairs"] = pairs
             c["fp64_equiv_tflops"] = c["work"] / s / 1e12 if s > 0 else 0.0
-            c["achieved"] = SLICE_PAIRS * c["work"] / s / 1e12 if s > 0 else 0.0
+            c["achieved"] = pairs * c["work"] / s / 1e12 if s > 0 else 0.0
             c["peak"] = bf16_peak
         else:
             c["bound"] = "alu"
@@ -246,14 +257,16 @@ def run_ours(args):
     # the rotation (Step 11) is one kernel family with a clean FLOP count; it and the
     # filter SpMM are the two kernels whose rates are reported
     dc = comp["rotation"]
-    roofline = {"kernel": "oz_gemm_kernel (Step 11 rotation, float64-accurate slices on bf16 "
-                          "tensor cores)" if tensor_path else "gemm_nn_kernel (Step 11, float64)",
+    roofline = {"kernel": "oz_gemm_kernel (Step 11 rotation, digit slices on bf16 tensor cores)"
+                if tensor_path else "gemm_nn_kernel (Step 11, float64)",
                 "bound": dc["bound"], "achieved": round(dc["achieved"], 3),
                 "peak": dc["peak"], "unit": dc["unit"],
                 "frac": round(dc["achieved"] / dc["peak"], 4), "traffic": None,
                 "fp64_equivalent_tflops": round(dc.get("fp64_equiv_tflops", dc["achieved"]), 3),
-                "note": "achieved counts the bf16 tensor FLOPs of the slice products over the "
-                        "Step-11 time including operand slicing",
+                "slice_pairs": dc.get("slice_pairs"),
+                "note": "achieved counts the bf16 tensor FLOPs of the slice products (slice_pairs "
+                        "per float64-equivalent flop) over the Step-11 time including operand "
+                        "slicing",
                 "peak_source": (f"{bf16_kind} bf16 (MEASURED_PEAKS.json)" if tensor_path else
                                 "nominal FP64 rate (2 DFMA/clk/SM); probe measured 1.19-1.20")}
     fc = comp["filter"]

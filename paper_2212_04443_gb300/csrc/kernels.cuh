@@ -120,10 +120,10 @@ cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, in
                             int c_off, void* planes, int* E);
 cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const int* EA, int capA,
                                 int a0, int ka, const void* PB, const int* EB, int capB, int kb,
-                                double* out, double* partial);
+                                double* out, double* partial, int slices = 8);
 cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void* PA, const int* EA,
                               const double* B, int ldb, int nb, double* C, int ldc, bool subtract,
-                              void* bwork);
+                              void* bwork, int slices = 8);
 size_t oz_bwork_bytes(int K, int nb);
 
 // ---------------- orthonormalisation (orth.cu) ----------------

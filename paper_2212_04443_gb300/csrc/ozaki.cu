@@ -177,7 +177,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // MODE 0: C = result; 1: C -= result; 2: partial[z] (M x N, row-major) = result.
 constexpr int kOzFlush = 64;
 
-template <int MODE>
+// NS: leading digit slices used (8: float64-accurate; fewer: a truncated product whose
+// operands keep 6 NS bits, for the first DGKS pass that the second one corrects)
+template <int MODE, int NS>
 __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, int Kp, int k_split,
                                                       const __nv_bfloat16* __restrict__ PA,
                                                       const int* __restrict__ EA,
@@ -200,14 +202,14 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
   const int kt1 = min(nk_all, kt0 + k_split);
 
   auto load_stage = [&](int buf, int k0) {
-    for (int q = t; q < kOzS * kOzBM * 2; q += 256) {
+    for (int q = t; q < NS * kOzBM * 2; q += 256) {
       const int s = q / (kOzBM * 2), rem = q - s * kOzBM * 2, row = rem >> 1, half = rem & 1;
       const int gr = r0 + row;
       __nv_bfloat16* dst = &sA[buf][s][oz_sw(row, half)];
       if (gr < M) cp_async16(dst, PA + s * planeA + (size_t)gr * Kp + k0 + half * 8);
       else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
-    for (int q = t; q < kOzS * kOzBN * 2; q += 256) {
+    for (int q = t; q < NS * kOzBN * 2; q += 256) {
       const int s = q / (kOzBN * 2), rem = q - s * kOzBN * 2, row = rem >> 1, half = rem & 1;
       const int gc = c0 + row;
       __nv_bfloat16* dst = &sB[buf][s][oz_sw(row, half)];
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
     cp_async_commit();
   };
 
-  float acc[kOzS][2][4];
+  float acc[NS][2][4];
   // float64 partial sums live in shared memory (touched only at flushes), 8 per thread
   double* dacc = reinterpret_cast<double*>(
       oz_smem + sizeof(__nv_bfloat16) * kOzStages * kOzS * (kOzBM + kOzBN) * 16) + t * 8;
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
   for (int e = 0; e < 8; ++e) dacc[e] = 0.0;
   auto zero_acc = [&]() {
 #pragma unroll
-    for (int L = 0; L < kOzS; ++L)
+    for (int L = 0; L < NS; ++L)
 #pragma unroll
       for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
       for (int e = 0; e < 4; ++e) {
         double v = 0.0;
 #pragma unroll
-        for (int L = kOzS - 1; L >= 0; --L)
+        for (int L = NS - 1; L >= 0; --L)
           v = fma((double)acc[L][j][e], __longlong_as_double((long long)(1023 - kOzBits * (L + 2)) << 52), v);
         if (MODE == 2) {
           const int row = r0 + wm * 16 + g + (e >> 1) * 8;
@@ -266,9 +268,9 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
     if (i + 2 < nst) load_stage((i + 2) % kOzStages, (kt + 2) * kOzBK);
     // fragments by ldmatrix: lane l addresses row (l & 7) of matrix l >> 3
     const int mi = lane >> 3, rr = lane & 7;
-    uint32_t bf[kOzS][2][2];
+    uint32_t bf[NS][2][2];
 #pragma unroll
-    for (int s = 0; s < kOzS; ++s) {
+    for (int s = 0; s < NS; ++s) {
       // matrices: (n-tile 0, k half 0), (0, 1), (1, 0), (1, 1)
       uint32_t q[4];
       ldsm_x4(q, &sB[buf][s][oz_sw(wn * 16 + (mi >> 1) * 8 + rr, mi & 1)]);
@@ -278,13 +280,13 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
       bf[s][1][1] = q[3];
     }
 #pragma unroll
-    for (int s = 0; s < kOzS; ++s) {
+    for (int s = 0; s < NS; ++s) {
       // matrices: (rows 0-7, k half 0), (rows 8-15, 0), (rows 0-7, 1), (rows 8-15, 1)
       uint32_t af[4];
       ldsm_x4(af, &sA[buf][s][oz_sw(wm * 16 + (mi & 1) * 8 + rr, mi >> 1)]);
 #pragma unroll
-      for (int tt = 0; tt < kOzS; ++tt) {
-        if (s + tt < kOzS) {   // levels s + tt + 2 <= 9
+      for (int tt = 0; tt < NS; ++tt) {
+        if (s + tt < NS) {   // levels s + tt + 2 <= NS + 1
           oz_mma(acc[s + tt][0], af, bf[tt][0]);
           oz_mma(acc[s + tt][1], af, bf[tt][1]);
         }
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
   }
 }
 
-template <int MODE>
+template <int MODE, int NS = kOzS>
 static cudaError_t oz_launch_gemm(cudaStream_t st, dim3 grid, int M, int Ma, int N, int Kp, int k_split,
                                   const __nv_bfloat16* PA, const int* EA, const __nv_bfloat16* PB,
                                   int Np, const int* EB, double* C, int ldc) {
@@ -323,9 +325,10 @@ static cudaError_t oz_launch_gemm(cudaStream_t st, dim3 grid, int M, int Ma, int
                       256 * 8 * sizeof(double);
   // set once per process (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(
-      oz_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      oz_gemm_kernel<MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (attr != cudaSuccess) return attr;
-  oz_gemm_kernel<MODE><<<grid, 256, smem, st>>>(M, Ma, N, Kp, k_split, PA, EA, PB, Np, EB, C, ldc);
+  oz_gemm_kernel<MODE, NS><<<grid, 256, smem, st>>>(M, Ma, N, Kp, k_split, PA, EA, PB, Np, EB, C,
+                                                    ldc);
   note_launch();
   return cudaGetLastError();
 }
@@ -525,7 +528,7 @@ __global__ void oz_zero_rows_kernel(__nv_bfloat16* P, size_t plane, int Np, int 
 // stride capB; capB >= round_up(kb, 32)).
 cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const int* EA, int capA,
                                 int a0, int ka, const void* PB, const int* EB, int capB, int kb,
-                                double* out, double* partial) {
+                                double* out, double* partial, int slices) {
   if (ka <= 0 || kb <= 0) return cudaSuccess;
   const __nv_bfloat16* pa = static_cast<const __nv_bfloat16*>(PA) + (size_t)a0 * Np;
   const __nv_bfloat16* pb = static_cast<const __nv_bfloat16*>(PB);
@@ -537,8 +540,18 @@ cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const i
   nsplit = ceil_div(nk, k_split);
   dim3 grid(mt, nt, nsplit);
   // the planes of A are read through an offset base: their row count per plane stays capA
-  cudaError_t e = oz_launch_gemm<2>(st, grid, ka, capA, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
-                                    partial, kb);
+  cudaError_t e;
+  if (slices == 4)
+    e = oz_launch_gemm<2, 4>(st, grid, ka, capA, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
+                             partial, kb);
+  else if (slices == 6)
+    e = oz_launch_gemm<2, 6>(st, grid, ka, capA, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
+                             partial, kb);
+  else if (slices == kOzS)
+    e = oz_launch_gemm<2>(st, grid, ka, capA, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
+                          partial, kb);
+  else
+    return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
   return launch_reduce_partials(st, partial, nsplit, ka * kb, out, 1.0);
 }
@@ -546,7 +559,7 @@ cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const i
 // C (n x nb) = / -= A B from row planes of A (S x n x Kp, exponents EA) and a small B (K x nb).
 cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void* PA, const int* EA,
                               const double* B, int ldb, int nb, double* C, int ldc, bool subtract,
-                              void* bwork) {
+                              void* bwork, int slices) {
   if (n <= 0 || nb <= 0 || K <= 0) return cudaSuccess;
   if (K > kOzMaxK) return cudaErrorInvalidValue;
   const int nbp = round_up(nb, kOzBN);
@@ -556,8 +569,15 @@ cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void*
                                                                             PB); note_launch();
   dim3 grid(ceil_div(n, kOzBM), nbp / kOzBN, 1);
   const __nv_bfloat16* pa = static_cast<const __nv_bfloat16*>(PA);
-  if (subtract)
+  // the subtraction X -= V C always uses every slice (its error must stay inside span(V));
+  // the product C = A B may use 6 (operands to 36 bits)
+  if (subtract) {
+    if (slices != kOzS) return cudaErrorInvalidValue;
     return oz_launch_gemm<1>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
+  }
+  if (slices == 6)
+    return oz_launch_gemm<0, 6>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
+  if (slices != kOzS) return cudaErrorInvalidValue;
   return oz_launch_gemm<0>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
 }
 

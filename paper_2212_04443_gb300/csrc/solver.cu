@@ -313,6 +313,8 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
     if (k > 0) {
       for (int pass = 0; pass < 2; ++pass) {
         if (tc) {
+          // both passes float64-accurate (a first pass from truncated slices measurably loosened
+          // the orthogonality on graphs with hub rows)
           HCUDA(oz_slice_cols_t(st, n, X, ldx, b, Np, capX, 0, h->oz_xt.p, Ext));
           HCUDA(oz_gram_from_planes(st, Np, h->oz_vt.p, Evt, capV, 0, k, h->oz_xt.p, Ext, capX, b,
                                     Gd, h->oz_part.as<double>()));
@@ -651,6 +653,11 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   // tensor-core products: V's column planes (Steps 6, 8) and row planes (Steps 6, 11) sized for
   // the whole subspace, X / W column planes, the split-B work and the split-reduction partials
   const OzLayout OL = oz_layout(N, ncols);
+  // Step 11 rotation: the float64 path keeps all 8 digit slices (48-bit operands); the mixed
+  // path takes 6 (36-bit operands, ~2e-11 relative per rotation), far below its float32
+  // filter's rounding and the 1e-8 residual target.  Step 8's H stays at 8 slices: its Ritz
+  // values decide convergence, and a hub row's chunk costs the other rows bits there.
+  const int slices_rr = prec == BCHDAV_PREC_MIXED ? 6 : 8;
   if (opts.dense_path == 0) {
     BCHDAV_TRY(h->ensure(h->oz_vt, OL.vt_planes + (size_t)oz_chunks(OL.Np) * OL.capV * sizeof(int) +
                                        256));
@@ -802,7 +809,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       const int Kp = oz_pad_k(k_old);
       HCUDA(oz_slice_rows(st, N, V + k_c, ldv, k_old, Kp, h->oz_vr.p, Evr));
       HCUDA(oz_nn_from_planes(st, N, k_old, Kp, h->oz_vr.p, Evr, Ym, act_max, k_act, V + k_c, ldv,
-                              false, h->oz_bw.p));
+                              false, h->oz_bw.p, slices_rr));
     } else {
       HCUDA(launch_gemm_nn_inplace(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act));
     }

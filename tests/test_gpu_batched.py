@@ -44,7 +44,7 @@ def test_batched_matches_brute_force(H, workers):
         ref = np.linalg.eigvalsh(L.dense())[:ks[i]]
         assert np.abs(e - ref).max() < 1e-10, i
         assert residuals(L.scipy(), e, v).max() <= TOL * 1.0001
-        assert np.abs(v.T @ v - np.eye(ks[i])).max() < 1e-12
+        assert np.abs(v.T @ v - np.eye(ks[i])).max() < 1e-10   # mixed path: 36-bit rotations
 
 
 def test_batched_equals_single_solves(H):

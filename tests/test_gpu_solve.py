@@ -33,14 +33,17 @@ def oracle_solve(g, k, b, m, act_max, v0_seed=0, **kw):
     return L, r
 
 
-def check_pairs(L, ev, V, k):
+def check_pairs(L, ev, V, k, orth=1e-12):
+    """orth: 1e-12 for the float64 path; the mixed path rotates its basis with 36-bit operands
+    (about 2e-11 relative per rotation), so its eigenvectors are orthonormal to ~1e-10 and its
+    Ritz values carry errors of the same order (the spectrum bound [0, 2] is checked to it)."""
     A = L.scipy()
     assert ev.shape == (k,) and V.shape == (L.n, k)
     assert np.all(np.diff(ev) >= -1e-14)
-    assert ev.min() > -1e-12 and ev.max() < 2 + 1e-12
+    assert ev.min() > -orth and ev.max() < 2 + orth
     res = residuals(A, ev, V)
     assert res.max() <= TOL * 1.0001, res.max()
-    assert np.abs(V.T @ V - np.eye(k)).max() < 1e-12
+    assert np.abs(V.T @ V - np.eye(k)).max() < orth
 
 
 CASES = [
@@ -113,7 +116,7 @@ def test_long_rows_solve_matches_brute_force(H):
     for prec in (0, 1):
         ev, V, info, _ = gpu_solve(H, g, 10, 5, 11, 30, precision=prec)
         assert info.status == 0
-        check_pairs(L, ev, V, 10)
+        check_pairs(L, ev, V, 10, orth=1e-12 if prec == 0 else 1e-10)
         assert np.abs(ev - ref[:10]).max() < 1e-10
 
 
@@ -168,7 +171,7 @@ def test_mixed_precision_reaches_tol(H):
     ev64, V64, i64, _ = gpu_solve(H, g, k, b, m, act)
     ev32, V32, i32, _ = gpu_solve(H, g, k, b, m, act, precision=P.PREC_MIXED)
     assert i64.status == 0 and i32.status == 0
-    check_pairs(L, ev32, V32, k)
+    check_pairs(L, ev32, V32, k, orth=1e-10)
     assert np.abs(ev32 - ev64).max() <= 1e-10
 
 
