@@ -260,10 +260,11 @@ cudaError_t launch_eigh(cudaStream_t st, int n, const double* H, int ldh, double
 // at the end with their columns of V.
 
 constexpr int kJacThreads = 256;
+constexpr int kJacPre = 4;   // items per thread whose operands are loaded ahead of the angles
 constexpr int kJacMaxSweeps = 40;
 
 struct JacLayout {
-  double *A, *V, *red;
+  double *A, *V, *red, *ang;
   int* status;
 };
 
@@ -273,18 +274,49 @@ __host__ __device__ inline JacLayout jac_layout(double* w, int n) {
   L.A = w;
   L.V = L.A + (size_t)np * np;
   L.red = L.V + (size_t)np * np;   // [2][grid] partial sums
-  L.status = reinterpret_cast<int*>(L.red + 2 * 4 * kSMs + 8);
+  L.ang = L.red + 2 * 4 * kSMs;     // [2][np / 2][3] angle inputs (a_pp, a_qq, a_pq) by round parity
+  L.status = reinterpret_cast<int*>(L.ang + 3 * (size_t)np + 8);
   return L;
 }
 
 size_t eigh_fast_work_doubles(int n) {
   const size_t np = (size_t)(n + (n & 1));
-  return 2 * np * np + 2 * 4 * kSMs + 16;
+  return 2 * np * np + 2 * 4 * kSMs + 3 * np + 16;
 }
 
 // player at circle position `pos` in round r (n_pad players, player 0 fixed)
 __device__ __forceinline__ int jac_player(int pos, int r, int np) {
   return pos == 0 ? 0 : 1 + (pos - 1 + r) % (np - 1);
+}
+// circle position of player x in round r (inverse of jac_player)
+__device__ __forceinline__ int jac_pos(int x, int r, int np) {
+  if (x == 0) return 0;
+  int t = (x - 1 - r) % (np - 1);
+  if (t < 0) t += np - 1;
+  return t + 1;
+}
+// position of a player in the next round: everyone but player 0 moves one place back on the
+// circle (position 1 wraps to np - 1)
+__device__ __forceinline__ int jac_next_pos(int pos, int np) {
+  return pos == 0 ? 0 : (pos == 1 ? np - 1 : pos - 1);
+}
+
+// Entry (x, y) of A, just rotated in round r, with next-round positions px, py: if round
+// r + 1 needs it to compute a rotation angle (a diagonal entry of one of its pairs, or a
+// pair's off-diagonal entry), store it in that round's angle-input slots.  The slots of a
+// round are written only in the round before and read only in that round (double buffered by
+// parity), so no CTA can read a value that another CTA is rewriting in the same round.
+__device__ __forceinline__ void jac_note_next(double* __restrict__ ang, int x, int y, int px,
+                                              int py, double v, int r, int np, int wbuf) {
+  const int half = np / 2;
+  const int kx = px < half ? px : np - 1 - px;
+  double* slot = ang + (size_t)wbuf * 3 * half + 3 * kx;
+  if (x == y) {
+    const int partner = jac_player(np - 1 - px, r + 1, np);
+    slot[x < partner ? 0 : 1] = v;
+  } else if (x < y && px + py == np - 1) {
+    slot[2] = v;
+  }
 }
 
 __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const double* __restrict__ H,
@@ -300,6 +332,8 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
   double* sn = sj + half;     // half
   int* pp = reinterpret_cast<int*>(sj + 2 * half);   // half
   int* qq = pp + half;                               // half
+  int* npp = qq + half;                              // half: next-round position of pp[k]
+  int* nqq = npp + half;                             // half: next-round position of qq[k]
   __shared__ double s_red[33];
   __shared__ int s_flag;
   const int t = threadIdx.x;
@@ -314,6 +348,21 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
     if (i < n && j < n) a = (i <= j) ? H[(size_t)i * ldh + j] : H[(size_t)j * ldh + i];
     A[idx] = a;
     V[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  // angle inputs of round 0, straight from H
+  for (long long k = gtid; k < half; k += gstride) {
+    int p = jac_player((int)k, 0, np), q = jac_player(np - 1 - (int)k, 0, np);
+    if (p > q) {
+      const int x = p;
+      p = q;
+      q = x;
+    }
+    auto h = [&](int i, int j) {
+      return (i < n && j < n) ? ((i <= j) ? H[(size_t)i * ldh + j] : H[(size_t)j * ldh + i]) : 0.0;
+    };
+    L.ang[3 * k] = h(p, p);
+    L.ang[3 * k + 1] = h(q, q);
+    L.ang[3 * k + 2] = h(p, q);
   }
   // ||A||_F^2 for the stopping threshold
   double loc = 0.0;
@@ -332,6 +381,44 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
   int status = 1;
   for (int sweep = 0; sweep < kJacMaxSweeps; ++sweep) {
     for (int r = 0; r < np - 1; ++r) {
+      const int rbuf = (int)(((long long)sweep * (np - 1) + r) & 1);   // angle inputs read now
+      // The pairs of round r are fixed by r alone, so each thread first loads the entries its
+      // (at most kJacPre) items will rotate, then the angles are computed while those loads
+      // are in flight; the arithmetic is that of one rotation at a time per entry.
+      const long long nblk = (long long)half * half;
+      const long long nitems = nblk + (long long)np * half;
+      double pre[kJacPre][4];
+      int ppre[kJacPre][4];
+#pragma unroll
+      for (int u = 0; u < kJacPre; ++u) {
+        const long long idx = gtid + u * gstride;
+        ppre[u][0] = -1;
+        if (idx >= nitems) continue;
+        if (idx < nblk) {
+          const int K = (int)(idx / half), Lb = (int)(idx - (long long)K * half);
+          int p1 = jac_player(K, r, np), q1 = jac_player(np - 1 - K, r, np);
+          int p2 = jac_player(Lb, r, np), q2 = jac_player(np - 1 - Lb, r, np);
+          if (p1 > q1) { const int x = p1; p1 = q1; q1 = x; }
+          if (p2 > q2) { const int x = p2; p2 = q2; q2 = x; }
+          ppre[u][0] = (int)(p1 * np + p2);
+          ppre[u][1] = (int)(p1 * np + q2);
+          ppre[u][2] = (int)(q1 * np + p2);
+          ppre[u][3] = (int)(q1 * np + q2);
+          pre[u][0] = A[ppre[u][0]];
+          pre[u][1] = A[ppre[u][1]];
+          pre[u][2] = A[ppre[u][2]];
+          pre[u][3] = A[ppre[u][3]];
+        } else {
+          const long long j = idx - nblk;
+          const int row = (int)(j / half), K = (int)(j - (long long)row * half);
+          int p = jac_player(K, r, np), q = jac_player(np - 1 - K, r, np);
+          if (p > q) { const int x = p; p = q; q = x; }
+          ppre[u][0] = (int)(row * np + p);
+          ppre[u][1] = (int)(row * np + q);
+          pre[u][0] = V[ppre[u][0]];
+          pre[u][1] = V[ppre[u][1]];
+        }
+      }
       // rotations of this round, computed identically by every CTA
       for (int k = t; k < half; k += kJacThreads) {
         int p = jac_player(k, r, np), q = jac_player(np - 1 - k, r, np);
@@ -342,11 +429,18 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
         }
         pp[k] = p;
         qq[k] = q;
+        {
+          // positions this round: k holds player(k), np - 1 - k holds the other
+          const int pos_p = (p == jac_player(k, r, np)) ? k : np - 1 - k;
+          npp[k] = jac_next_pos(pos_p, np);
+          nqq[k] = jac_next_pos(np - 1 - pos_p, np);
+        }
         double c = 1.0, s = 0.0;
         if (q < n) {
-          const double apq = A[(size_t)p * np + q];
+          const double* in = L.ang + (size_t)rbuf * 3 * half + 3 * k;
+          const double apq = in[2];
           if (apq != 0.0) {
-            const double app = A[(size_t)p * np + p], aqq = A[(size_t)q * np + q];
+            const double app = in[0], aqq = in[1];
             const double theta = (aqq - app) / (2.0 * apq);
             const double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
             c = 1.0 / sqrt(fma(tt, tt, 1.0));
@@ -358,38 +452,68 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
       }
       __syncthreads();
       // A <- J^T A J on the 2x2 blocks (K, L); V <- V J on the column pairs
-      const long long nblk = (long long)half * half;
-      for (long long idx = gtid; idx < nblk + (long long)np * half; idx += gstride) {
+      auto apply = [&](long long idx, double (&x)[4], const int (&off)[4], bool loaded) {
         if (idx < nblk) {
           const int K = (int)(idx / half), Lb = (int)(idx - (long long)K * half);
-          const int p1 = pp[K], q1 = qq[K], p2 = pp[Lb], q2 = qq[Lb];
           const double c1 = cs[K], s1 = sn[K], c2 = cs[Lb], s2 = sn[Lb];
-          if (s1 == 0.0 && s2 == 0.0) continue;
-          double* a11 = A + (size_t)p1 * np + p2;
-          double* a12 = A + (size_t)p1 * np + q2;
-          double* a21 = A + (size_t)q1 * np + p2;
-          double* a22 = A + (size_t)q1 * np + q2;
-          const double x11 = *a11, x12 = *a12, x21 = *a21, x22 = *a22;
-          // rows: J1^T X
-          const double y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
-          const double y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
-          // columns: (J1^T X) J2
-          *a11 = c2 * y11 - s2 * y12;
-          *a12 = s2 * y11 + c2 * y12;
-          *a21 = c2 * y21 - s2 * y22;
-          *a22 = s2 * y21 + c2 * y22;
-          if (K == Lb) *a12 = *a21 = 0.0;   // the pair entry this rotation annihilates
+          const int p1 = pp[K], q1 = qq[K], p2 = pp[Lb], q2 = qq[Lb];
+          int o[4] = {off[0], off[1], off[2], off[3]};
+          if (!loaded) {
+            o[0] = p1 * np + p2;
+            o[1] = p1 * np + q2;
+            o[2] = q1 * np + p2;
+            o[3] = q1 * np + q2;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) x[e] = A[o[e]];
+          }
+          double z[4] = {x[0], x[1], x[2], x[3]};
+          if (!(s1 == 0.0 && s2 == 0.0)) {
+            const double x11 = x[0], x12 = x[1], x21 = x[2], x22 = x[3];
+            // rows: J1^T X
+            const double y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+            const double y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+            // columns: (J1^T X) J2
+            z[0] = c2 * y11 - s2 * y12;
+            z[1] = s2 * y11 + c2 * y12;
+            z[2] = c2 * y21 - s2 * y22;
+            z[3] = s2 * y21 + c2 * y22;
+            if (K == Lb) z[1] = z[2] = 0.0;   // the pair entry this rotation annihilates
+#pragma unroll
+            for (int e = 0; e < 4; ++e) A[o[e]] = z[e];
+          }
+          {
+            const int np1 = npp[K], nq1 = nqq[K], np2 = npp[Lb], nq2 = nqq[Lb];
+            jac_note_next(L.ang, p1, p2, np1, np2, z[0], r, np, rbuf ^ 1);
+            jac_note_next(L.ang, p1, q2, np1, nq2, z[1], r, np, rbuf ^ 1);
+            jac_note_next(L.ang, q1, p2, nq1, np2, z[2], r, np, rbuf ^ 1);
+            jac_note_next(L.ang, q1, q2, nq1, nq2, z[3], r, np, rbuf ^ 1);
+          }
         } else {
           const long long j = idx - nblk;
           const int row = (int)(j / half), K = (int)(j - (long long)row * half);
           const double c = cs[K], s = sn[K];
-          if (s == 0.0) continue;
-          double* vp = V + (size_t)row * np + pp[K];
-          double* vq = V + (size_t)row * np + qq[K];
-          const double xp = *vp, xq = *vq;
-          *vp = c * xp - s * xq;
-          *vq = s * xp + c * xq;
+          if (s == 0.0) return;
+          int o0 = off[0], o1 = off[1];
+          if (!loaded) {
+            o0 = row * np + pp[K];
+            o1 = row * np + qq[K];
+            x[0] = V[o0];
+            x[1] = V[o1];
+          }
+          const double xp = x[0], xq = x[1];
+          V[o0] = c * xp - s * xq;
+          V[o1] = s * xp + c * xq;
         }
+      };
+#pragma unroll
+      for (int u = 0; u < kJacPre; ++u) {
+        const long long idx = gtid + u * gstride;
+        if (idx < nitems) apply(idx, pre[u], ppre[u], true);
+      }
+      for (long long idx = gtid + kJacPre * gstride; idx < nitems; idx += gstride) {
+        double x[4];
+        const int off[4] = {0, 0, 0, 0};
+        apply(idx, x, off, false);
       }
       grid.sync();
     }
@@ -432,12 +556,12 @@ cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, d
   if (n <= 32) return launch_eigh(st, n, H, ldh, D, Y, ldy, work, status);
   if (n > 1024) return cudaErrorInvalidValue;
   const int np = n + (n & 1);
-  const size_t smem = (size_t)(np / 2) * (2 * sizeof(double) + 2 * sizeof(int));
+  const size_t smem = (size_t)(np / 2) * (2 * sizeof(double) + 4 * sizeof(int));
   // one wave of co-resident blocks (thread-safe static initialisation)
   static const int max_blocks = []() {
     int per_sm = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, kJacThreads,
-                                                      12 * 1024) != cudaSuccess) {
+                                                      16 * 1024) != cudaSuccess) {
       cudaGetLastError();
       return 1;
     }
