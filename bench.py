@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--dense-path", type=int, default=0, choices=[0, 1],
-                    help="0: float64-accurate tensor-core products; 1: float64 FMA kernels")
+    ap.add_argument("--dense-path", type=int, default=0, choices=[0, 1, 2],
+                    help="0: slice products on warp-level mma; 1: float64 FMA kernels; "
+                         "2: row-operand slice products on tcgen05")
     return ap.parse_args()
 
 
@@ -235,7 +236,7 @@ def run_ours(args):
         "orthonormalisation": dict(ms=info.ms["orth"], work=orth_flops(hist, n, b), unit="TFLOP/s"),
         "rayleigh_quotient": dict(ms=info.ms["h"], work=h_flops(hist, n, b), unit="TFLOP/s"),
     }
-    tensor_path = dense_path == 0
+    tensor_path = dense_path != 1
     bf16_peak, bf16_kind = load_bf16_peak()
     for name, c in comp.items():
         s = c["ms"] / 1e3

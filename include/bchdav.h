@@ -69,8 +69,10 @@ typedef struct {
   int32_t dim_max;          /* 0: min(max(act_max + 2b, k + 30), N)  (Sec. 4 defaults) */
   int32_t itmax;            /* 0: 1000 outer iterations */
   int32_t precision;        /* bchdav_precision */
-  int32_t dense_path;       /* 0: float64-accurate tensor-core products (split into bf16 slices)
-                               for Steps 6 and 11; 1: plain float64 FMA kernels */
+  int32_t dense_path;       /* 0: float64-accurate tensor-core products (split into bf16 slices,
+                               warp-level mma) for Steps 6, 8 and 11; 1: plain float64 FMA
+                               kernels; 2: as 0 with the row-operand products (Step 6 update,
+                               Step 11 rotation) on tcgen05 (tensor memory accumulators) */
   uint64_t seed;            /* seed of the random vectors the method draws (Philox4x32-10) */
   const double* v_init;     /* optional N x k_init initial block (Algorithm 2, V_init) */
   int32_t k_init;

@@ -36,12 +36,21 @@ struct bchdav_handle_s {
   DevBuf Rres, mix;   // mixed path: residual block of Step 12, per-column filter coefficients
   DevBuf oz;          // slices of the float64-accurate tensor-core products
   DevBuf oz_vt, oz_vr, oz_xt, oz_bw, oz_part;   // cached planes: V by columns, V by rows, X by columns
+  DevBuf tc_err;                                // set by a tensor-core kernel whose wait expired
   // long-row schedule of the CSR matrix in use (rows over the segment threshold)
   DevBuf lg_cnt, lg_off, lg_tiles, lg_row, lg_pseg;
   bchdav::SpmmLong lg;
   DevBuf gnn, gnn_opt, gnn_w;   // start-block network: activations, optimiser state, Ritz step
   const bchdav::SpmmLong* long_rows() const { return lg.n_seg > 0 ? &lg : nullptr; }
   std::vector<bchdav_iter_record> history;
+  // filter SpMM schedules found by timing (block size of the row kernel per matrix and width)
+  struct SpmmTuneEntry {
+    const int* rowptr;
+    int n;
+    long long nnz;
+    int b, vsize, threads;
+  };
+  std::vector<SpmmTuneEntry> spmm_tune;
   // worker handles of bchdav_solve_batched (own streams, cooperative grids capped at one block)
   std::vector<bchdav_handle_s*> workers;
   int batch_workers = 8;
@@ -105,7 +114,7 @@ struct bchdav_handle_s {
 
   void release_all() {
     DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
-                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part,
+                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part, &tc_err,
                      &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w};
     lg = bchdav::SpmmLong();
     for (DevBuf* b : all) b->release();

@@ -36,7 +36,7 @@ cudaError_t launch_spmm_axpby(cudaStream_t st, int n, const int* rowptr, const i
                               const T* val, const T* X, int ldx, int b, T* Y, int ldy,
                               const T* Z, int ldz, T alpha, T beta, T gamma,
                               const T* R = nullptr, int ldr = 0, const T* delta = nullptr,
-                              const SpmmLong* lg = nullptr);
+                              const SpmmLong* lg = nullptr, int threads = 256);
 
 // Residual of Step 12: R = A V - V diag(d) into Rout (n x b, ldr >= b; required), then
 // per-CTA partial sums of r_j^2 and v_j^2 in partial[cta * 2b + {j, b + j}]; the CTA count
@@ -124,6 +124,15 @@ cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const i
 cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void* PA, const int* EA,
                               const double* B, int ldb, int nb, double* C, int ldc, bool subtract,
                               void* bwork, int slices = 8);
+// The same product C = / -= A B from A's row planes on the tcgen05 tensor cores (tc05.cu):
+// B (K x nb) is split here into planes of round_up(nb, 32 or 64) columns in bwork; err (device
+// int, may be NULL) is set when a bounded wait inside the kernel expires.
+cudaError_t oz_nn_from_planes_tc(cudaStream_t st, int n, int K, int Kp, const void* PA,
+                                 const int* EA, const double* B, int ldb, int nb, double* C,
+                                 int ldc, bool subtract, void* bwork, int slices, int* err);
+cudaError_t launch_tc_slice_nn(cudaStream_t st, int n, int nb, int Kp, const void* PA,
+                               const int* EA, const void* PB, int nbp, const int* EB, double* C,
+                               int ldc, bool subtract, int slices, int* err);
 size_t oz_bwork_bytes(int K, int nb);
 
 // ---------------- orthonormalisation (orth.cu) ----------------

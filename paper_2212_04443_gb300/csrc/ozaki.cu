@@ -581,9 +581,22 @@ cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void*
   return oz_launch_gemm<0>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
 }
 
+cudaError_t oz_nn_from_planes_tc(cudaStream_t st, int n, int K, int Kp, const void* PA,
+                                 const int* EA, const double* B, int ldb, int nb, double* C,
+                                 int ldc, bool subtract, void* bwork, int slices, int* err) {
+  if (n <= 0 || nb <= 0 || K <= 0) return cudaSuccess;
+  if (K > kOzMaxK) return cudaErrorInvalidValue;
+  const int nbp = nb <= 32 ? 32 : round_up(nb, 64);
+  __nv_bfloat16* PB = static_cast<__nv_bfloat16*>(bwork);
+  int* EB = reinterpret_cast<int*>(PB + (size_t)kOzS * nbp * Kp);
+  oz_split_cols_kernel<<<ceil_div((long long)nbp * 32, 256), 256, 0, st>>>(K, nb, B, ldb, Kp, nbp, EB,
+                                                                            PB); note_launch();
+  return launch_tc_slice_nn(st, n, nb, Kp, PA, EA, PB, nbp, EB, C, ldc, subtract, slices, err);
+}
+
 size_t oz_bwork_bytes(int K, int nb) {
-  return kOzS * (size_t)round_up(nb, kOzBN) * round_up(K, kOzBK) * sizeof(__nv_bfloat16) +
-         (size_t)round_up(nb, kOzBN) * sizeof(int) + 256;
+  const size_t nbp = (size_t)round_up(nb, 64);   // covers both slice-product kernels' padding
+  return kOzS * nbp * round_up(K, kOzBK) * sizeof(__nv_bfloat16) + nbp * sizeof(int) + 256;
 }
 
 }  // namespace bchdav

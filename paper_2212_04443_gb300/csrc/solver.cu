@@ -60,6 +60,47 @@ struct Timer {
   }
 };
 
+// Filter SpMM schedule: the row kernel's block size (rows per CTA) for this matrix and block
+// width, chosen by timing each candidate on the first call (the first filter step's own
+// buffers; every candidate computes every row the same way) and cached in the handle.  Small
+// graphs want small blocks (enough CTAs to cover the GPU); large ones fewer, larger blocks.
+template <typename F>
+bchdav_status spmm_schedule(bchdav_handle h, const bchdav_csr* A, int b, int vsize, F run,
+                            int* threads) {
+  for (const auto& e : h->spmm_tune)
+    if (e.rowptr == A->rowptr && e.n == A->n && e.nnz == A->nnz && e.b == b && e.vsize == vsize) {
+      *threads = e.threads;
+      return BCHDAV_OK;
+    }
+  cudaStream_t st = h->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HCUDA(cudaEventCreate(&e0));
+  HCUDA(cudaEventCreate(&e1));
+  const int cand[4] = {64, 128, 256, 512};
+  float best = 3.0e38f;
+  int best_t = 256;
+  cudaError_t err = cudaSuccess;
+  for (int c : cand) {
+    if ((err = run(c)) != cudaSuccess) break;   // warm
+    if ((err = cudaEventRecord(e0, st)) != cudaSuccess) break;
+    if ((err = run(c)) != cudaSuccess || (err = run(c)) != cudaSuccess) break;
+    if ((err = cudaEventRecord(e1, st)) != cudaSuccess) break;
+    if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((err = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+    if (ms < best) {
+      best = ms;
+      best_t = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HCUDA(err);
+  h->spmm_tune.push_back({A->rowptr, A->n, A->nnz, b, vsize, best_t});
+  *threads = best_t;
+  return BCHDAV_OK;
+}
+
 // ---------------- Algorithm 3 ----------------
 // Y = p_m(A) X.  prec MIXED: recurrence in float32 (val32 required).
 bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val32, const double* X,
@@ -79,10 +120,16 @@ bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val3
     float* T[4] = {h->F[0].as<float>(), h->F[1].as<float>(), h->F[2].as<float>(),
                    h->F[3].as<float>()};
     HCUDA(launch_f64_to_f32(st, n, b, X, ldx, T[0], ldb));
+    int thr = 256;
+    BCHDAV_TRY(spmm_schedule(h, A, b, 4, [&](int bs) {
+      return launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[0], ldb, b, T[1], ldb,
+                                      nullptr, 0, 1.f, 0.f, 0.f, nullptr, 0, nullptr,
+                                      h->long_rows(), bs);
+    }, &thr));
     // step 1: U = (A X - c X) sigma / e
     HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[0], ldb, b, T[1], ldb,
                                    nullptr, 0, (float)(sigma / e), (float)(-c * sigma / e), 0.f,
-                                   nullptr, 0, nullptr, h->long_rows()));
+                                   nullptr, 0, nullptr, h->long_rows(), thr));
     bytes += csr_bytes + 3.0 * n * b * sx;
     int prev = 0, cur = 1;
     for (int i = 2; i <= m; ++i) {
@@ -92,7 +139,7 @@ bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val3
       HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[cur], ldb, b, T[nxt],
                                      ldb, T[prev], ldb, (float)(2.0 * sigma1 / e),
                                      (float)(-2.0 * sigma1 * c / e), (float)(-sigma * sigma1),
-                                     nullptr, 0, nullptr, h->long_rows()));
+                                     nullptr, 0, nullptr, h->long_rows(), thr));
       bytes += csr_bytes + 4.0 * n * b * sx;
       prev = cur;
       cur = nxt;
@@ -106,9 +153,15 @@ bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val3
     int prevld = ldx;
     double* out = (m == 1) ? Y : T[0];
     int outld = (m == 1) ? ldy : ldb;
+    int thr = 256;
+    BCHDAV_TRY(spmm_schedule(h, A, b, 8, [&](int bs) {
+      return launch_spmm_axpby<double>(st, n, A->rowptr, A->colidx, A->val, X, ldx, b, T[1], ldb,
+                                       nullptr, 0, 1.0, 0.0, 0.0, nullptr, 0, nullptr,
+                                       h->long_rows(), bs);
+    }, &thr));
     HCUDA(launch_spmm_axpby<double>(st, n, A->rowptr, A->colidx, A->val, X, ldx, b, out, outld,
                                     nullptr, 0, sigma / e, -c * sigma / e, 0.0, nullptr, 0, nullptr,
-                                    h->long_rows()));
+                                    h->long_rows(), thr));
     bytes += csr_bytes + 3.0 * n * b * sx;
     const double* curp = out;
     int curld = outld;
@@ -128,7 +181,7 @@ bchdav_status run_filter(bchdav_handle h, const bchdav_csr* A, const float* val3
       HCUDA(launch_spmm_axpby<double>(st, n, A->rowptr, A->colidx, A->val, curp, curld, b, nxt,
                                       nxtld, prevp, prevld, 2.0 * sigma1 / e,
                                       -2.0 * sigma1 * c / e, -sigma * sigma1, nullptr, 0, nullptr,
-                                      h->long_rows()));
+                                      h->long_rows(), thr));
       bytes += csr_bytes + 4.0 * n * b * sx;
       prevp = curp;
       prevld = curld;
@@ -203,11 +256,17 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
   HCUDA(launch_mixed_inputs(st, n, b, X, ldx, any_res ? R : X, any_res ? ldr : ldx, src_d, T[0],
                             R32, ldb));
   const float* Rp = any_res ? R32 : nullptr;
+  int thr = 256;
+  BCHDAV_TRY(spmm_schedule(h, A, b, 4, [&](int bs) {
+    return launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[0], ldb, b, T[1], ldb,
+                                    nullptr, 0, 1.f, 0.f, 0.f, nullptr, 0, nullptr,
+                                    h->long_rows(), bs);
+  }, &thr));
   const double csr_bytes = 4.0 * (n + 1) + (double)A->nnz * 8.0;
   double bytes = 0.0;
   HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[0], ldb, b, T[1], ldb,
                                  nullptr, 0, (float)(sigma1 / e), (float)(-c * sigma1 / e), 0.f, Rp,
-                                 ldb, delta_d, h->long_rows()));
+                                 ldb, delta_d, h->long_rows(), thr));
   bytes += csr_bytes + (any_res ? 4.0 : 3.0) * n * b * 4.0;
   int prev = 0, cur = 1;
   for (int i = 2; i <= m; ++i) {
@@ -216,7 +275,7 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
     HCUDA(launch_spmm_axpby<float>(st, n, A->rowptr, A->colidx, val32, T[cur], ldb, b, T[nxt], ldb,
                                    T[prev], ldb, (float)(2.0 * sig[i] / e),
                                    (float)(-2.0 * sig[i] * c / e), (float)(-sig[i - 1] * sig[i]),
-                                   Rp, ldb, delta_d + (size_t)(i - 1) * 64, h->long_rows()));
+                                   Rp, ldb, delta_d + (size_t)(i - 1) * 64, h->long_rows(), thr));
     bytes += csr_bytes + (any_res ? 5.0 : 4.0) * n * b * 4.0;
     prev = cur;
     cur = nxt;
@@ -287,7 +346,7 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   // tensor-core path: slices of V (by columns for V^T X, by rows for X -= V C) are made once
   // and serve both passes and every retry; X is sliced by columns for each Gram product
   if (vt_valid) *vt_valid = 0;
-  const bool tc = dense_path == 0 && ozaki_nn_supported(std::max(k, 1));
+  const bool tc = (dense_path == 0 || dense_path == 2) && ozaki_nn_supported(std::max(k, 1));
   const OzLayout L = oz_layout(n, std::max(k, cap_cols));
   const int Np = L.Np, capV = L.capV, capX = oz_pad_cols(b);
   const int Kp = oz_pad_k(std::max(k, 1));
@@ -318,8 +377,12 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
           HCUDA(oz_slice_cols_t(st, n, X, ldx, b, Np, capX, 0, h->oz_xt.p, Ext));
           HCUDA(oz_gram_from_planes(st, Np, h->oz_vt.p, Evt, capV, 0, k, h->oz_xt.p, Ext, capX, b,
                                     Gd, h->oz_part.as<double>()));
-          HCUDA(oz_nn_from_planes(st, n, k, Kp, h->oz_vr.p, Evr, Gd, b, b, X, ldx, true,
-                                  h->oz_bw.p));
+          if (dense_path == 2)
+            HCUDA(oz_nn_from_planes_tc(st, n, k, Kp, h->oz_vr.p, Evr, Gd, b, b, X, ldx, true,
+                                       h->oz_bw.p, 8, h->tc_err.as<int>()));
+          else
+            HCUDA(oz_nn_from_planes(st, n, k, Kp, h->oz_vr.p, Evr, Gd, b, b, X, ldx, true,
+                                    h->oz_bw.p));
         } else {
           HCUDA(launch_gemm_tn_partial(st, n, V, ldv, k, X, ldx, b, h->part.as<double>(), chunks));
           HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, k * b, Gd, 1.0));
@@ -537,11 +600,11 @@ bchdav_status bchdav_gram(bchdav_handle h, int32_t n, const double* A, int32_t l
                           int32_t dense_path) {
   if (!h) return BCHDAV_ERR_ARG;
   if (n < 1 || ka < 1 || kb < 1 || lda < ka || ldb < kb || !A || !B || !out ||
-      (dense_path != 0 && dense_path != 1) || (size_t)ka * kb > 16 * 1024 * 1024) {
+      dense_path < 0 || dense_path > 2 || (size_t)ka * kb > 16 * 1024 * 1024) {
     h->set_error(BCHDAV_ERR_ARG, "gram: bad arguments");
     return BCHDAV_ERR_ARG;
   }
-  if (dense_path == 0) {
+  if (dense_path != 1) {
     BCHDAV_TRY(h->ensure(h->oz, ozaki_tn_work_bytes(n, ka, kb)));
     HCUDA(launch_ozaki_tn(h->stream, n, A, lda, ka, B, ldb, kb, out, h->oz.p));
   } else {
@@ -557,11 +620,29 @@ bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, 
                             const double* Y, int32_t ld_y, int32_t nb, int32_t dense_path) {
   if (!h) return BCHDAV_ERR_ARG;
   if (n < 1 || k < 1 || nb < 1 || nb > k || ldv < k || ld_y < nb || !V || !Y ||
-      (dense_path != 0 && dense_path != 1)) {
+      dense_path < 0 || dense_path > 2) {
     h->set_error(BCHDAV_ERR_ARG, "rotate: bad arguments");
     return BCHDAV_ERR_ARG;
   }
-  if (dense_path == 0 && ozaki_nn_supported(k)) {
+  if (dense_path == 2 && ozaki_nn_supported(k)) {
+    // tcgen05 slice product from V's row planes (in place: the planes hold all of V)
+    const int Kp = oz_pad_k(k);
+    BCHDAV_TRY(h->ensure(h->oz, oz_planes_bytes(n, Kp) + (size_t)n * sizeof(int) + 256));
+    BCHDAV_TRY(h->ensure(h->oz_bw, oz_bwork_bytes(k, nb)));
+    BCHDAV_TRY(h->ensure(h->tc_err, sizeof(int)));
+    int* E = reinterpret_cast<int*>(h->oz.as<char>() + oz_planes_bytes(n, Kp));
+    HCUDA(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), h->stream));
+    HCUDA(oz_slice_rows(h->stream, n, V, ldv, k, Kp, h->oz.p, E));
+    HCUDA(oz_nn_from_planes_tc(h->stream, n, k, Kp, h->oz.p, E, Y, ld_y, nb, V, ldv, false,
+                               h->oz_bw.p, 8, h->tc_err.as<int>()));
+    int flag = 0;
+    HCUDA(cudaMemcpyAsync(&flag, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    HCUDA(cudaStreamSynchronize(h->stream));
+    if (flag) {
+      h->set_error(BCHDAV_ERR_TIMEOUT, "rotate: a tensor-core wait expired");
+      return BCHDAV_ERR_TIMEOUT;
+    }
+  } else if (dense_path == 0 && ozaki_nn_supported(k)) {
     BCHDAV_TRY(h->ensure(h->oz, ozaki_nn_work_bytes(n, k, nb)));
     HCUDA(launch_ozaki_nn(h->stream, n, V, ldv, k, Y, ld_y, nb, V, ldv, false, h->oz.p));
   } else {
@@ -609,7 +690,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   if (k < 1 || k > N || b < 1 || b > 64 || m < 1 || act_max < 2 * b || act_max > N ||
       !(tol > 0) || !evals || !evecs || (prec != BCHDAV_PREC_FP64 && prec != BCHDAV_PREC_MIXED) ||
       (opts.k_init > 0 && (!opts.v_init || opts.ld_v_init < opts.k_init)) ||
-      (opts.dense_path != 0 && opts.dense_path != 1)) {
+      opts.dense_path < 0 || opts.dense_path > 2) {
     h->set_error(BCHDAV_ERR_ARG, "solve: invalid k, b, m, act_max, tol or options");
     return BCHDAV_ERR_ARG;
   }
@@ -658,7 +739,9 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   // filter's rounding and the 1e-8 residual target.  Step 8's H stays at 8 slices: its Ritz
   // values decide convergence, and a hub row's chunk costs the other rows bits there.
   const int slices_rr = prec == BCHDAV_PREC_MIXED ? 6 : 8;
-  if (opts.dense_path == 0) {
+  BCHDAV_TRY(h->ensure(h->tc_err, sizeof(int)));
+  HCUDA(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), st));
+  if (opts.dense_path != 1) {
     BCHDAV_TRY(h->ensure(h->oz_vt, OL.vt_planes + (size_t)oz_chunks(OL.Np) * OL.capV * sizeof(int) +
                                        256));
     BCHDAV_TRY(h->ensure(h->oz_vr, OL.vr_planes + (size_t)N * sizeof(int) + 256));
@@ -767,7 +850,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     k_sub += b;
     // Step 8: H(1:k_act, new) = V(:, k_c+1:k_sub)^T W_new, symmetrise
     tm_h.start(st);
-    if (opts.dense_path == 0) {
+    if (opts.dense_path != 1) {
       // V's column planes from Step 6 are still current for columns [0, vt_valid); slice the
       // rest of V(:, k_c+1:k_sub) (the new block) and W_new, then reduce over the N rows
       int* Evt = reinterpret_cast<int*>(h->oz_vt.as<char>() + OL.vt_planes);
@@ -802,14 +885,18 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     }
     // Step 11: rotation V(:, k_c+1 : k_c+k_act) = V(:, k_c+1 : k_c+k_old) Y(:, 1:k_act)
     tm_rot.start(st);
-    if (opts.dense_path == 0 && ozaki_nn_supported(k_old)) {
+    if (opts.dense_path != 1 && ozaki_nn_supported(k_old)) {
       // the row planes of Step 6 are stale (V gained a block); re-slice V(:, k_c+1:k_c+k_old)
       // into the same buffer, then V is overwritten in place (the planes hold all of A)
       int* Evr = reinterpret_cast<int*>(h->oz_vr.as<char>() + OL.vr_planes);
       const int Kp = oz_pad_k(k_old);
       HCUDA(oz_slice_rows(st, N, V + k_c, ldv, k_old, Kp, h->oz_vr.p, Evr));
-      HCUDA(oz_nn_from_planes(st, N, k_old, Kp, h->oz_vr.p, Evr, Ym, act_max, k_act, V + k_c, ldv,
-                              false, h->oz_bw.p, slices_rr));
+      if (opts.dense_path == 2)
+        HCUDA(oz_nn_from_planes_tc(st, N, k_old, Kp, h->oz_vr.p, Evr, Ym, act_max, k_act, V + k_c,
+                                   ldv, false, h->oz_bw.p, slices_rr, h->tc_err.as<int>()));
+      else
+        HCUDA(oz_nn_from_planes(st, N, k_old, Kp, h->oz_vr.p, Evr, Ym, act_max, k_act, V + k_c,
+                                ldv, false, h->oz_bw.p, slices_rr));
     } else {
       HCUDA(launch_gemm_nn_inplace(st, N, V + k_c, ldv, k_old, Ym, act_max, k_act));
     }
@@ -976,6 +1063,14 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   HCUDA(cudaStreamSynchronize(st));
   collect();
   tm_total.collect();
+  if (opts.dense_path == 2) {
+    int flag = 0;
+    HCUDA(cudaMemcpy(&flag, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      h->set_error(BCHDAV_ERR_TIMEOUT, "solve: a tensor-core wait expired");
+      return BCHDAV_ERR_TIMEOUT;
+    }
+  }
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->iters = it;

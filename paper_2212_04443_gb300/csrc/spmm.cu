@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) spmm_long_seg_kernel(
 // A group of tpr consecutive threads owns one row (groups may straddle warps); rpb rows per
 // CTA.  Rows longer than kLongRow read their segment sums instead of walking their nonzeros.
 template <typename T, int VW>
-__global__ void __launch_bounds__(256) spmm_axpby_kernel(
+__global__ void __launch_bounds__(512) spmm_axpby_kernel(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
     const T* __restrict__ val, const T* __restrict__ X, int ldx, int b, T* __restrict__ Y, int ldy,
     const T* __restrict__ Z, int ldz, T alpha, T beta, T gamma, const T* __restrict__ R, int ldr,
@@ -260,7 +260,8 @@ template <typename T, int VW>
 static cudaError_t spmm_rows_launch(cudaStream_t st, int n, const int* rowptr, const int* colidx,
                                     const T* val, const T* X, int ldx, int b, T* Y, int ldy,
                                     const T* Z, int ldz, T alpha, T beta, T gamma, const T* R,
-                                    int ldr, const T* delta, int tpr, const SpmmLong* lg) {
+                                    int ldr, const T* delta, int tpr, const SpmmLong* lg,
+                                    int threads) {
   const long long* seg_off = nullptr;
   const T* pseg = nullptr;
   if (lg != nullptr && lg->n_seg > 0) {
@@ -281,7 +282,9 @@ static cudaError_t spmm_rows_launch(cudaStream_t st, int n, const int* rowptr, c
     seg_off = lg->seg_off;
     pseg = ps;
   }
-  const int rpb = 256 / tpr;
+  // rows per CTA from the block size (64..512 threads; the caller's schedule, default 256)
+  const int bs = threads == 64 || threads == 128 || threads == 512 ? threads : 256;
+  const int rpb = std::max(1, bs / tpr);
   const int grid = ceil_div(n, rpb);
   spmm_axpby_kernel<T, VW><<<grid, rpb * tpr, 0, st>>>(n, rowptr, colidx, val, X, ldx, b, Y, ldy,
                                                        Z, ldz, alpha, beta, gamma, R, ldr, delta,
@@ -293,7 +296,7 @@ template <typename T>
 cudaError_t launch_spmm_axpby(cudaStream_t st, int n, const int* rowptr, const int* colidx,
                               const T* val, const T* X, int ldx, int b, T* Y, int ldy,
                               const T* Z, int ldz, T alpha, T beta, T gamma, const T* R, int ldr,
-                              const T* delta, const SpmmLong* lg) {
+                              const T* delta, const SpmmLong* lg, int threads) {
   if (n <= 0 || b <= 0) return cudaSuccess;
   int vw = pick_vw<T>(b, X, ldx, Y, ldy, Z, ldz);
   if (R != nullptr && vw > 1 && (((uintptr_t)R % (vw * sizeof(T))) != 0 || ldr % vw != 0)) vw = 1;
@@ -301,13 +304,13 @@ cudaError_t launch_spmm_axpby(cudaStream_t st, int n, const int* rowptr, const i
   if (tpr > 256 || (vw > 1 && tpr > 32)) return cudaErrorInvalidValue;
   if (vw == 1)
     return spmm_rows_launch<T, 1>(st, n, rowptr, colidx, val, X, ldx, b, Y, ldy, Z, ldz, alpha,
-                                  beta, gamma, R, ldr, delta, tpr, lg);
+                                  beta, gamma, R, ldr, delta, tpr, lg, threads);
   if (vw == 2)
     return spmm_rows_launch<T, 2>(st, n, rowptr, colidx, val, X, ldx, b, Y, ldy, Z, ldz, alpha,
-                                  beta, gamma, R, ldr, delta, tpr, lg);
+                                  beta, gamma, R, ldr, delta, tpr, lg, threads);
   if constexpr (sizeof(T) == 4)
     return spmm_rows_launch<T, 4>(st, n, rowptr, colidx, val, X, ldx, b, Y, ldy, Z, ldz, alpha,
-                                  beta, gamma, R, ldr, delta, tpr, lg);
+                                  beta, gamma, R, ldr, delta, tpr, lg, threads);
   return cudaErrorInvalidValue;
 }
 
@@ -315,11 +318,11 @@ template cudaError_t launch_spmm_axpby<double>(cudaStream_t, int, const int*, co
                                                const double*, const double*, int, int, double*,
                                                int, const double*, int, double, double, double,
                                                const double*, int, const double*,
-                                               const SpmmLong*);
+                                               const SpmmLong*, int);
 template cudaError_t launch_spmm_axpby<float>(cudaStream_t, int, const int*, const int*,
                                               const float*, const float*, int, int, float*, int,
                                               const float*, int, float, float, float, const float*,
-                                              int, const float*, const SpmmLong*);
+                                              int, const float*, const SpmmLong*, int);
 
 // ---------------- residual norms (Step 12) ----------------
 // R = A V - V diag(d) through the row kernel (all rows in flight at once; the product's

@@ -211,10 +211,33 @@ def test_deterministic_repeat(H):
 
 
 def test_dense_paths_agree(H):
-    """Tensor-core split products and plain float64 FMA kernels give the same solve."""
+    """Tensor-core split products (warp-level mma, or tcgen05 for the row-operand products) and
+    plain float64 FMA kernels give the same solve."""
     g = synth.sbm_edges(20000, 20, d_in=14, d_out=2, seed=13)
     a = gpu_solve(H, g, 20, 10, 13, 50, dense_path=0)
     b = gpu_solve(H, g, 20, 10, 13, 50, dense_path=1)
-    assert a[2].status == 0 and b[2].status == 0
-    assert [h.k_c for h in a[3]] == [h.k_c for h in b[3]]
+    c = gpu_solve(H, g, 20, 10, 13, 50, dense_path=2)
+    assert a[2].status == 0 and b[2].status == 0 and c[2].status == 0
+    assert [h.k_c for h in a[3]] == [h.k_c for h in b[3]] == [h.k_c for h in c[3]]
     assert np.abs(a[0] - b[0]).max() <= 1e-12
+    assert np.abs(c[0] - b[0]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tcgen05_path_matches_oracle(H, prec):
+    """dense_path 2 on the oracle-parity case and on a hub graph, both precisions."""
+    g = synth.sbm_edges(20000, 20, d_in=14, d_out=2, seed=13)
+    ev, V, info, hist = gpu_solve(H, g, 20, 10, 13, 50, precision=prec, dense_path=2)
+    L, r = oracle_solve(g, 20, 10, 13, 50)
+    assert info.status == 0
+    check_pairs(L, ev, V, 20, orth=1e-12 if prec == 0 else 1e-10)
+    assert np.abs(ev - r.evals).max() <= 1e-10
+    if prec == 0:
+        assert info.iters == r.iters
+    g = synth.disjoint_union(synth.star_edges(3000), synth.rmat_edges(11, seed=4),
+                             synth.sbm_edges(1500, 3, d_in=8, d_out=1, seed=2))
+    L = oracle_csr(g)
+    ev, V, info, _ = gpu_solve(H, g, 10, 5, 11, 30, precision=prec, dense_path=2)
+    assert info.status == 0
+    check_pairs(L, ev, V, 10, orth=1e-12 if prec == 0 else 1e-10)
+    assert np.abs(ev - np.linalg.eigvalsh(L.dense())[:10]).max() < 1e-10

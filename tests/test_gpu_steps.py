@@ -243,10 +243,12 @@ def test_eigh_diagonal_plus_border(H):
     assert np.abs(S @ Y - Y * D).max() < 1e-13
 
 
-@pytest.mark.parametrize("n,k,nb", [(50000, 300, 240), (1001, 77, 45), (4000, 16, 16), (777, 448, 5)])
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("n,k,nb", [(50000, 300, 240), (1001, 77, 45), (4000, 16, 16), (777, 448, 5),
+                                    (130001, 96, 70)])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_rotate_matches_float64(H, n, k, nb, path):
-    """Step 11 product V(:, :nb) = V(:, :k) Y, tensor-core split (path 0) and float64 FMA (path 1)."""
+    """Step 11 product V(:, :nb) = V(:, :k) Y: tensor-core split on warp-level mma (path 0) or
+    on tcgen05 with tensor-memory accumulators (path 2), and float64 FMA (path 1)."""
     import torch
     rng = synth.rng(n + k)
     V = rng.standard_normal((n, k)) / np.sqrt(n)
