@@ -157,6 +157,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_nn_kernel(
     c0 = (int)(tile % n_ct) * BN;
     r0 = (int)(tile / n_ct) * kTcM;
   };
+  // thread 0's step cursors (no divisions on the issue path): the producer's next step and the
+  // tile it lies in
+  int pk = 0, pr0 = 0, pc0 = 0;
+  long long ptile = blockIdx.x;
+  auto advance = [&](int& k, long long& tile, int& r0, int& c0) {
+    if (++k == nk) {
+      k = 0;
+      tile += gridDim.x;
+      c0 += (int)gridDim.x % n_ct * BN;   // tile advances by gridDim.x: carry into rows
+      r0 += (int)(gridDim.x / n_ct) * kTcM;
+      if (c0 >= n_ct * BN) {
+        c0 -= n_ct * BN;
+        r0 += kTcM;
+      }
+    }
+  };
+  {
+    int k0;
+    origin(0, pr0, pc0, k0);
+  }
+  // descriptor bases per stage (the slice offsets are added to the address field)
+  unsigned long long dA[kTcStages], dB[kTcStages];
+#pragma unroll
+  for (int i = 0; i < kTcStages; ++i) {
+    dA[i] = tc_desc(smem_u32(sA + (size_t)i * kTcAStage), kTcM * 16, 128);
+    dB[i] = tc_desc(smem_u32(sB + (size_t)i * kTcBStage), BN * 16, 128);
+  }
   // thread 0 only: copies of step p into stage p % kTcStages
   long long issued = 0, consumed = 0;
   unsigned bar_commits = 0;   // commits on tile_bar so far
@@ -168,8 +195,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_nn_kernel(
       fail = true;
       return;
     }
-    int r0, c0, kt;
-    origin(p, r0, c0, kt);
+    const int r0 = pr0, c0 = pc0, kt = pk;
+    advance(pk, ptile, pr0, pc0);
     const unsigned fb = smem_u32(full + st);
     mbar_expect(fb, kStageBytes);
     const unsigned a0 = smem_u32(sA + (size_t)st * kTcAStage);
@@ -183,28 +210,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_nn_kernel(
       }
     issued = p + 1;
   };
-  auto consume = [&](long long g) {
+  auto consume = [&](long long g, int kt) {
     const int st = (int)(g % kTcStages);
     if (!mbar_wait(smem_u32(full + st), (unsigned)((g / kTcStages) & 1))) {
       fail = true;
       return;
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    int r0, c0, kt;
-    origin(g, r0, c0, kt);
-    const unsigned a0 = smem_u32(sA + (size_t)st * kTcAStage);
-    const unsigned b0 = smem_u32(sB + (size_t)st * kTcBStage);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      // A slice s: core matrices 128 B apart along M, the k halves 2 KB apart
-      const unsigned long long ad = tc_desc(a0 + (unsigned)(s * 2) * (kTcM * 16), kTcM * 16, 128);
+      // A slice s: core matrices 128 B apart along M, the k halves 2 KB apart (the address
+      // field of the descriptor counts 16-byte units)
+      const unsigned long long ad = dA[st] + (unsigned long long)((s * 2 * kTcM * 16) >> 4);
 #pragma unroll
       for (int u = 0; u < NS; ++u) {
         if (s + u < NS) {
-          const unsigned long long bd = tc_desc(b0 + (unsigned)(u * 2) * (BN * 16), BN * 16, 128);
+          const unsigned long long bd = dB[st] + (unsigned long long)((u * 2 * BN * 16) >> 4);
           // level s + u starts fresh at a tile's first k step with its first pair (0, level)
-          const int acc = (kt > 0 || s > 0) ? 1 : 0;
-          tc_mma(tmem + (unsigned)((s + u) * BN), ad, bd, tc_idesc<BN>(), acc);
+          tc_mma(tmem + (unsigned)((s + u) * BN), ad, bd, tc_idesc<BN>(), (kt > 0 || s > 0) ? 1 : 0);
         }
       }
     }
@@ -218,7 +241,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_nn_kernel(
         for (long long p = 0; p < kTcStages - 1 && p < total && !fail; ++p) produce(p);
       for (int kt = 0; kt < nk && !fail; ++kt) {
         const long long g = (long long)j * nk + kt;
-        consume(g);
+        consume(g, kt);
         if (!fail && g + kTcStages - 1 < total) produce(g + kTcStages - 1);
       }
       if (fail) *s_fail = 1;
