@@ -148,6 +148,10 @@ def slice_pairs(S):
     return S * (S + 1) // 2
 
 
+# DRAM bytes per Step-11 rotation launch (mixed path, 1M-node SBM): ncu capture at N = 200,000
+# scaled by N (profiles/oz_gemm_rotation_traffic.md); valid for the kernel as captured
+ROTATION_TRAFFIC_BYTES = {"mixed": 3.33e9}
+
 # pairs per float64-equivalent flop of each component, by path
 PAIRS = {
     "f64": {"rotation": 36, "rayleigh_quotient": 36, "orthonormalisation": 36},
@@ -262,7 +266,11 @@ def run_ours(args):
                 if tensor_path else "gemm_nn_kernel (Step 11, float64)",
                 "bound": dc["bound"], "achieved": round(dc["achieved"], 3),
                 "peak": dc["peak"], "unit": dc["unit"],
-                "frac": round(dc["achieved"] / dc["peak"], 4), "traffic": None,
+                "frac": round(dc["achieved"] / dc["peak"], 4),
+                "traffic": (ROTATION_TRAFFIC_BYTES.get("mixed") if tensor_path and dense_path == 0
+                            and prec == P.PREC_MIXED and args.workload == "sbm1m" else None),
+                "traffic_note": "DRAM bytes per Step-11 launch: ncu capture at N=200,000 scaled "
+                                "by N (profiles/oz_gemm_rotation_traffic.md)",
                 "fp64_equivalent_tflops": round(dc.get("fp64_equiv_tflops", dc["achieved"]), 3),
                 "slice_pairs": dc.get("slice_pairs"),
                 "note": "achieved counts the bf16 tensor FLOPs of the slice products (slice_pairs "

@@ -194,7 +194,12 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
       oz_smem + sizeof(__nv_bfloat16) * kOzStages * kOzS * kOzBM * 16);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int wm = warp & 3, wn = warp >> 2;
-  const int r0 = blockIdx.x * kOzBM, c0 = blockIdx.y * kOzBN;
+  // MODE 0/1 (A's rows are the output rows, B small): a flat grid with the column tiles of a row
+  // tile adjacent, so that they find A's tile in L2 (one DRAM pass over A); MODE 2: (M tile,
+  // N tile, k split)
+  const int nct = Np / kOzBN;
+  const int r0 = MODE == 2 ? blockIdx.x * kOzBM : (int)(blockIdx.x / nct) * kOzBM;
+  const int c0 = MODE == 2 ? blockIdx.y * kOzBN : (int)(blockIdx.x % nct) * kOzBN;
   const size_t planeA = (size_t)Ma * Kp, planeB = (size_t)Np * Kp;
   const int g = lane >> 2, tig = lane & 3;
   const int nk_all = Kp / kOzBK;
@@ -357,7 +362,7 @@ cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, in
   oz_split_rows_kernel<<<16 * kSMs, 256, 0, st>>>(n, A, lda, K, Kp, EA, PA); note_launch();
   oz_split_cols_kernel<<<ceil_div((long long)nbp * 32, 256), 256, 0, st>>>(K, nb, B, ldb, Kp, nbp, EB,
                                                                             PB); note_launch();
-  dim3 grid(ceil_div(n, kOzBM), nbp / kOzBN, 1);
+  dim3 grid((unsigned)((long long)ceil_div(n, kOzBM) * (nbp / kOzBN)), 1, 1);
   const int ks = Kp / kOzBK;
   if (subtract) return oz_launch_gemm<1>(st, grid, n, n, nb, Kp, ks, PA, EA, PB, nbp, EB, C, ldc);
   return oz_launch_gemm<0>(st, grid, n, n, nb, Kp, ks, PA, EA, PB, nbp, EB, C, ldc);
@@ -567,7 +572,7 @@ cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void*
   int* EB = reinterpret_cast<int*>(PB + (size_t)kOzS * nbp * Kp);
   oz_split_cols_kernel<<<ceil_div((long long)nbp * 32, 256), 256, 0, st>>>(K, nb, B, ldb, Kp, nbp, EB,
                                                                             PB); note_launch();
-  dim3 grid(ceil_div(n, kOzBM), nbp / kOzBN, 1);
+  dim3 grid((unsigned)((long long)ceil_div(n, kOzBM) * (nbp / kOzBN)), 1, 1);
   const __nv_bfloat16* pa = static_cast<const __nv_bfloat16*>(PA);
   // the subtraction X -= V C always uses every slice (its error must stay inside span(V));
   // the product C = A B may use 6 (operands to 36 bits)

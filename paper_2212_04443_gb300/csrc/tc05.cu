@@ -20,6 +20,8 @@
 // wait on an mbarrier is bounded: on expiry the CTA records an error, stops issuing, and still
 // waits (also bounded) for the copies and products it issued before it frees the tensor memory
 // and returns.
+#include <cstdlib>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -77,8 +79,9 @@ __device__ __forceinline__ void tc_commit(unsigned mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
-  for (long long i = 0; i < kTcSpin; ++i) {
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity,
+                                          long long limit = kTcSpin) {
+  for (long long i = 0; i < limit; ++i) {
     unsigned done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -110,7 +113,7 @@ template <int MODE, int NS, int BN>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_nn_kernel(
     const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n,
     int nb, int Kp, const int* __restrict__ EA, const int* __restrict__ EB,
-    double* __restrict__ C, int ldc, int* __restrict__ err) {
+    double* __restrict__ C, int ldc, int* __restrict__ err, int expire_first_wait) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* sA = tc_smem;                                      // [stage][s][h] 2 KB each
   unsigned char* sB = tc_smem + (size_t)kTcStages * kTcAStage;      // [stage][s][h] BN x 16 B
@@ -118,7 +121,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_nn_kernel(
       reinterpret_cast<unsigned long long*>(sB + (size_t)kTcStages * kTcBStage);
   unsigned long long* empty = full + kTcStages;
   unsigned long long* tile_bar = empty + kTcStages;
-  unsigned* tslot = reinterpret_cast<unsigned*>(tile_bar + 1);
+  unsigned long long* never = tile_bar + 1;   // nothing arrives on it (error-path test)
+  unsigned* tslot = reinterpret_cast<unsigned*>(never + 1);
   int* s_fail = reinterpret_cast<int*>(tslot + 1);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_nn_kernel(
   const long long total = (long long)my_tiles * nk;   // (tile, k step) pairs of this CTA
 
   if (t == 0) {
-    for (int i = 0; i < 2 * kTcStages + 1; ++i)
+    for (int i = 0; i < 2 * kTcStages + 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(full + i)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     *s_fail = 0;
@@ -212,6 +216,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_nn_kernel(
   };
   auto consume = [&](long long g, int kt) {
     const int st = (int)(g % kTcStages);
+    // expire_first_wait (tests only): the first wait polls a barrier nothing arrives on, briefly,
+    // so that the error path below runs without any fault
+    if (expire_first_wait && g == 0 && !mbar_wait(smem_u32(never), 0, 1000)) {
+      fail = true;
+      return;
+    }
     if (!mbar_wait(smem_u32(full + st), (unsigned)((g / kTcStages) & 1))) {
       fail = true;
       return;
@@ -360,8 +370,11 @@ cudaError_t tc_launch(cudaStream_t st, int n, int nb, int Kp, const void* PA, co
     return v > 0 ? v : kSMs;
   }();
   dim3 grid((unsigned)(tiles < sms ? tiles : sms));
+  // BCHDAV_TEST_EXPIRE_TC_WAIT=1 (tests of the timeout path only): see expire_first_wait
+  const char* env = getenv("BCHDAV_TEST_EXPIRE_TC_WAIT");
+  const int expire = env && env[0] == '1' ? 1 : 0;
   tc_slice_nn_kernel<MODE, NS, BN><<<grid, kTcThreads, kTcSmem, st>>>(mA, mB, n, nb, Kp, EA, EB, C,
-                                                                      ldc, err);
+                                                                      ldc, err, expire);
   note_launch();
   return cudaGetLastError();
 }

@@ -309,3 +309,24 @@ def test_gram_per_chunk_precision_with_hub_entries(H, path):
         bound += min(ch, n - r0) * 2.0 ** -45 * a[:, None] * b[None, :]
     assert np.all(err <= bound + fp)
     assert np.all(err[2] <= 1e-3 * np.sqrt(n) * 2.0 ** -28 + fp[2])
+
+
+def test_tcgen05_wait_timeout_reports_and_recovers(H, monkeypatch):
+    """A bounded wait inside the tcgen05 kernel that expires (forced by a test switch: the first
+    wait polls a barrier nothing arrives on) returns BCHDAV_ERR_TIMEOUT without faulting; the
+    same handle then computes correctly."""
+    import torch
+    import paper_2212_04443_gb300 as P
+    rng = synth.rng(5)
+    n, k, nb = 20000, 64, 40
+    V = rng.standard_normal((n, k)) / np.sqrt(n)
+    Y = np.ascontiguousarray(np.linalg.qr(rng.standard_normal((k, k)))[0][:, :nb])
+    Yd = torch.from_numpy(Y).cuda()
+    monkeypatch.setenv("BCHDAV_TEST_EXPIRE_TC_WAIT", "1")
+    with pytest.raises(P.BchdavError) as ei:
+        H.rotate(torch.from_numpy(V.copy()).cuda(), Yd, nb, dense_path=2)
+    assert ei.value.status == -6
+    monkeypatch.delenv("BCHDAV_TEST_EXPIRE_TC_WAIT")
+    Vd = torch.from_numpy(V.copy()).cuda()
+    H.rotate(Vd, Yd, nb, dense_path=2)
+    assert np.abs(to_np(Vd)[:, :nb] - V @ Y).max() <= 1e-13 * np.abs(V @ Y).max()
