@@ -21,7 +21,9 @@ paper states:
 * ``philox``     the Philox4x32-10 counter-based generator (Salmon et al.,
                  SC 2011) that draws replacement vectors inside the method;
 * ``gnn``        the learned start block (an extension feeding V_init): network,
-                 subspace-alignment loss, its gradient, Adam, Ritz ordering.
+                 subspace-alignment loss, its gradient, Adam, Ritz ordering;
+* ``cluster``    Algorithm 1, Steps 4-5: row normalisation of the eigenvectors and
+                 Lloyd's k-means on the rows; adjusted Rand index and NMI.
 
 Pins (tests/test_oracle_*.py, run with ``-m "not gpu"``): closed-form spectra
 of cycles, paths, hypercubes, complete and complete-bipartite graphs and their
@@ -38,3 +40,4 @@ from .philox import philox4x32_10, uniform_pm_half  # noqa: F401
 from .dgks import dgks_orthonormalize  # noqa: F401
 from .bchdav import bchdav, BchdavResult, default_params, relative_residuals  # noqa: F401
 from . import gnn  # noqa: F401
+from . import cluster  # noqa: F401

@@ -63,6 +63,11 @@ def gnn_random_features(n: int, d_r: int, seed: int) -> np.ndarray:
     return rng(seed).standard_normal((n, d_r)).astype(np.float32)
 
 
+def kmeans_first(n: int, seed: int) -> int:
+    """Index of the first k-means seed: one uniform draw from [0, n)."""
+    return int(rng(seed).integers(0, n))
+
+
 def gnn_init(d_in: int, width: int, k: int, layers: int = 3, seed: int = 0) -> np.ndarray:
     """Flat float32 initial parameters of the start-block network: every weight matrix
     (fan_in x fan_out) normal with standard deviation sqrt(1 / fan_in), biases zero, in the
