@@ -20,14 +20,14 @@ caller); dmin_i = +inf; for j = 1..c-1: dmin_i = min(dmin_i, dist(X_i, X_{s_{j-1
 s_j = argmax_i dmin_i, the lowest i on ties.
 
 Lloyd's iteration.  Centroids start at C_j = X_{s_j} (float64).  Assignment: label_i = argmin_j
-dist(X_i, float32(C_j)), the lowest j on ties.  Update: q_id = round-half-even(X_id * 2^40) as a
-64-bit integer (exact: |X_id| <= 1), Q_jd = sum of q_id over the members of cluster j (integer
-sum, the same in any order), C_jd = (float64(Q_jd) / count_j) * 2^-40; a cluster without
-members keeps its centroid.  The fixed-point sum differs from the float64 mean by less than
-2^-40 per coordinate, far below the float32 resolution of the assignment; it makes the
-centroids independent of the summation order.  Rounds: the first assignment is round 1; each
-update followed by an assignment is one more round; stop when an assignment changes no label
-or after ``max_rounds`` rounds.
+dist(X_i, float32(C_j)), the lowest j on ties.  Update: q_id = round-half-even(X_id * 2^36) as a
+64-bit integer, Q_jd = sum of q_id over the members of cluster j (an integer sum, the same in
+any order; it cannot overflow while |X_id| <= 1, as for Step 4's rows, and N < 2^27),
+C_jd = (float64(Q_jd) / count_j) * 2^-36; a cluster without members keeps its centroid.  The
+fixed-point mean differs from the float64 mean by at most 2^-37 per coordinate, far below the
+float32 resolution of the assignment; it makes the centroids independent of the summation
+order.  Rounds: the first assignment is round 1; each update followed by an assignment is one
+more round; stop when an assignment changes no label or after ``max_rounds`` rounds.
 
 Also the two scores used against planted labels: the adjusted Rand index (Hubert and Arabie,
 1985) and normalised mutual information with the arithmetic-mean normalisation.
@@ -36,7 +36,7 @@ from __future__ import annotations
 
 import numpy as np
 
-Q_SCALE = 2.0 ** 40
+Q_SCALE = 2.0 ** 36
 
 
 def normalize_rows(V: np.ndarray) -> np.ndarray:
