@@ -7,10 +7,10 @@ the nodes' features.  Step 5 clusters the features, with k-means named as one ch
 fixes neither the k-means variant, its seeding nor its arithmetic, so this module is the
 definition that the CUDA path reproduces bit for bit:
 
-Features (Step 4).  nrm_i = sqrt(s_i) with s_i = sum over d = 0..k-1, in that order, of
-V_id * V_id in float64 (each product and sum rounded, no fused multiply-add);
-X_id = float32(V_id / nrm_i) (float64 division, then round to nearest float32); a row with
-nrm_i = 0 stays zero.
+Features (Step 4).  s_i = sum over d = 0..k-1, in that order, of V_id * V_id in float64 (each
+product and sum rounded, no fused multiply-add); r_i = 1 / sqrt(s_i) (one float64 square root
+and one division per row); X_id = float32(V_id * r_i) (float64 product, then round to nearest
+float32); a row with s_i = 0 stays zero.
 
 Distance.  dist(x, c) in float32: acc = 0; for d = 0..k-1: diff = x_d - c_d;
 acc = acc + diff * diff, every operation rounded to float32, no fused multiply-add.
@@ -45,10 +45,10 @@ def normalize_rows(V: np.ndarray) -> np.ndarray:
     s = np.zeros(V.shape[0])
     for d in range(V.shape[1]):
         s = s + V[:, d] * V[:, d]
-    nrm = np.sqrt(s)
     out = np.zeros_like(V)
-    nz = nrm > 0
-    out[nz] = V[nz] / nrm[nz, None]
+    nz = s > 0
+    r = 1.0 / np.sqrt(s[nz])
+    out[nz] = V[nz] * r[:, None]
     return out
 
 

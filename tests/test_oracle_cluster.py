@@ -10,12 +10,17 @@ from oracle import cluster as C
 
 
 def test_normalize_rows_closed_form():
-    V = np.array([[3.0, 4.0], [0.0, 0.0], [-2.0, 0.0], [1e-200, 1e-200]])
+    V = np.array([[3.0, 4.0], [0.0, 0.0], [-2.0, 0.0], [1e-200, 1e-200], [0.0, 4.0],
+                  [1.0, 1.0]])
     X = C.normalize_rows(V)
-    assert np.array_equal(X[0], [0.6, 0.8])
+    assert np.allclose(X[0], [0.6, 0.8], rtol=2.3e-16, atol=0)   # 1/5 is not exact: 1 ulp
     assert np.array_equal(X[1], [0.0, 0.0])          # zero row stays zero
     assert np.array_equal(X[2], [-1.0, 0.0])
     assert np.array_equal(X[3], [0.0, 0.0])          # squares underflow: norm 0, row zero
+    assert np.array_equal(X[4], [0.0, 1.0])          # r = 1/4 exact
+    # 1/sqrt(2) rounded once, then the product: the float64 nearest 2^-1/2 here
+    assert X[5, 0] == X[5, 1] == 1.0 / np.sqrt(2.0)
+    assert C.features(V)[0].tolist() == [np.float32(0.6), np.float32(0.8)]
 
 
 def test_normalize_rows_unit_length_and_direction():
