@@ -268,6 +268,57 @@ bchdav_status bchdav_gnn_start_block(bchdav_handle h, const bchdav_csr* A, const
                                      int32_t d_r, const float* theta, int32_t width, int32_t k,
                                      double* V0, double* ritz);
 
+/* ---- Algorithm 1, Steps 4-5: spectral clustering of the eigenvectors ------ */
+
+/* The paper's Algorithm 1 normalises each row of the eigenvector block (Step 4) and
+ * clusters the rows (Step 5), naming k-means as one method; it fixes neither the variant nor
+ * its arithmetic.  These calls implement Lloyd's k-means with farthest-first seeding in a
+ * fixed arithmetic, so that labels, seeds and centroids are bit-reproducible and independent
+ * of the launch shape:
+ *   features   X(i, d) = float32(V(i, d) / sqrt(s_i)), s_i the float64 sum over d in order of
+ *              V(i, d)^2 (separate multiply and add); a zero row stays zero;
+ *   distance   acc = 0; acc = acc + (x_d - c_d)^2 over d in order, float32, no fused
+ *              multiply-add;
+ *   seeding    s_0 = first; s_j = the node with the largest min_{l<j} dist(X_i, X_{s_l}),
+ *              the lowest index on ties (farthest-first traversal);
+ *   assignment the nearest float32(C_j), the lowest j on ties;
+ *   update     C_j = float64(Q_j) / count_j * 2^-36 with Q_j the 64-bit integer sum of
+ *              round-half-even(X_i * 2^36) over the members (order-independent; exact while
+ *              |X| <= 1 and n < 2^27); a cluster without members keeps its centroid;
+ *   rounds     the first assignment is round 1, each update + assignment one more; stop
+ *              when an assignment changes no label or after max_rounds rounds.
+ * Features are stored transposed: Xt is dim x n, row-major, leading dimension ldx >= n
+ * (element (d, i) at Xt[d * ldx + i]).  Limits: 1 <= n < 2^27, 1 <= dim <= 512,
+ * 1 <= n_clusters <= n; otherwise BCHDAV_ERR_ARG and nothing is enqueued. */
+
+/* Step 4: V is n x dim row-major (ld ldv >= dim, float64), e.g. the evecs of bchdav_solve;
+ * writes Xt.  Enqueue only. */
+bchdav_status bchdav_row_normalize(bchdav_handle h, int32_t n, int32_t dim, const double* V,
+                                   int64_t ldv, float* Xt, int64_t ldx);
+
+/* Farthest-first seeds: seeds[0..n_clusters-1] (device int32) from the node `first` in
+ * [0, n).  Enqueue only (n_clusters - 1 passes over Xt). */
+bchdav_status bchdav_kmeans_seed(bchdav_handle h, int32_t n, int32_t dim, const float* Xt,
+                                 int64_t ldx, int32_t n_clusters, int32_t first, int32_t* seeds);
+
+/* Step 5: Lloyd's k-means from the nodes seeds[] (device int32, each in [0, n); a seed
+ * outside that range gives BCHDAV_ERR_ARG after the call's work has drained).  labels: n
+ * int32 (device); centroids: n_clusters x dim row-major float64 (device, may be NULL), the
+ * centroids of the final assignment; rounds: HOST int32 (may be NULL).  Synchronises the
+ * handle's stream once per round (the stopping test). */
+bchdav_status bchdav_kmeans(bchdav_handle h, int32_t n, int32_t dim, const float* Xt,
+                            int64_t ldx, int32_t n_clusters, const int32_t* seeds,
+                            int32_t max_rounds, int32_t* labels, double* centroids,
+                            int32_t* rounds);
+
+/* Steps 4 and 5 in one call: features of V into the handle's workspace, farthest-first seeds
+ * from `first`, Lloyd's k-means.  seeds (device, n_clusters int32) and centroids may be
+ * NULL. */
+bchdav_status bchdav_spectral_cluster(bchdav_handle h, int32_t n, int32_t dim, const double* V,
+                                      int64_t ldv, int32_t n_clusters, int32_t first,
+                                      int32_t max_rounds, int32_t* labels, double* centroids,
+                                      int32_t* seeds, int32_t* rounds);
+
 /* ---- allocation-free variant (no counterpart in the paper) --------------- */
 
 /* bchdav_eigh for callers that cannot allocate device memory when they call

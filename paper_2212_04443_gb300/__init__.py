@@ -36,6 +36,7 @@ EXPORTED_SYMBOLS = [
     "bchdav_eigh_noalloc", "bchdav_solve_batched", "bchdav_set_batch_workers",
     "bchdav_launch_count", "bchdav_gnn_n_params", "bchdav_gnn_forward", "bchdav_gnn_loss_grad",
     "bchdav_gnn_train", "bchdav_gnn_start_block", "bchdav_release_workspace",
+    "bchdav_row_normalize", "bchdav_kmeans_seed", "bchdav_kmeans", "bchdav_spectral_cluster",
 ]
 
 
@@ -133,6 +134,11 @@ def lib() -> C.CDLL:
         "bchdav_rotate": (i32, [p, i32, p, i32, i32, p, i32, i32, i32]),
         "bchdav_gram": (i32, [p, i32, p, i32, i32, p, i32, i32, p, i32]),
         "bchdav_eigh_noalloc": (i32, [i32, p, i32, p, p, i32, p]),
+        "bchdav_row_normalize": (i32, [p, i32, i32, p, i64, p, i64]),
+        "bchdav_kmeans_seed": (i32, [p, i32, i32, p, i64, i32, i32, p]),
+        "bchdav_kmeans": (i32, [p, i32, i32, p, i64, i32, p, i32, p, p, C.POINTER(C.c_int32)]),
+        "bchdav_spectral_cluster": (i32, [p, i32, i32, p, i64, i32, i32, i32, p, p, p,
+                                          C.POINTER(C.c_int32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -394,6 +400,61 @@ class Handle:
                                                   self._f32(theta), width, k, _ptr(V0),
                                                   _ptr(ritz)))
         return V0, ritz
+
+    # ---- Algorithm 1, Steps 4-5: spectral clustering
+    def row_normalize(self, V, Xt=None):
+        """Transposed float32 features (dim x n) of the float64 row-major block V (n x dim)."""
+        import torch
+        assert V.dtype == torch.float64 and V.is_cuda and V.stride(1) == 1
+        n, dim = V.shape
+        if Xt is None:
+            Xt = torch.empty((dim, n), dtype=torch.float32, device=V.device)
+        self._check(self.L.bchdav_row_normalize(self.h, n, dim, _ptr(V), V.stride(0), _ptr(Xt),
+                                                Xt.stride(0)))
+        return Xt
+
+    def kmeans_seed(self, Xt, n_clusters: int, first: int):
+        import torch
+        dim, n = Xt.shape
+        seeds = torch.empty(n_clusters, dtype=torch.int32, device=Xt.device)
+        self._check(self.L.bchdav_kmeans_seed(self.h, n, dim, self._f32r(Xt), Xt.stride(0),
+                                              n_clusters, first, _ptr(seeds)))
+        return seeds
+
+    def kmeans(self, Xt, seeds, max_rounds: int = 100):
+        """(labels int32 [n], centroids float64 [c, dim], rounds)."""
+        import torch
+        dim, n = Xt.shape
+        c = int(seeds.numel())
+        assert seeds.dtype == torch.int32 and seeds.is_cuda
+        labels = torch.empty(n, dtype=torch.int32, device=Xt.device)
+        cent = torch.empty((c, dim), dtype=torch.float64, device=Xt.device)
+        r = C.c_int32(0)
+        self._check(self.L.bchdav_kmeans(self.h, n, dim, self._f32r(Xt), Xt.stride(0), c,
+                                         _ptr(seeds), max_rounds, _ptr(labels), _ptr(cent),
+                                         C.byref(r)))
+        return labels, cent, r.value
+
+    def spectral_cluster(self, V, n_clusters: int, first: int, max_rounds: int = 100):
+        """Steps 4-5 on the eigenvector block V (n x dim float64): (labels, centroids, seeds,
+        rounds)."""
+        import torch
+        assert V.dtype == torch.float64 and V.is_cuda and V.stride(1) == 1
+        n, dim = V.shape
+        labels = torch.empty(n, dtype=torch.int32, device=V.device)
+        cent = torch.empty((n_clusters, dim), dtype=torch.float64, device=V.device)
+        seeds = torch.empty(n_clusters, dtype=torch.int32, device=V.device)
+        r = C.c_int32(0)
+        self._check(self.L.bchdav_spectral_cluster(self.h, n, dim, _ptr(V), V.stride(0),
+                                                   n_clusters, first, max_rounds, _ptr(labels),
+                                                   _ptr(cent), _ptr(seeds), C.byref(r)))
+        return labels, cent, seeds, r.value
+
+    @staticmethod
+    def _f32r(t):
+        import torch
+        assert t.dtype == torch.float32 and t.is_cuda and t.stride(1) == 1
+        return _ptr(t)
 
     def _info(self, st, info) -> SolveInfo:
         ms = dict(total=info.ms_total, filter=info.ms_filter, orth=info.ms_orth,

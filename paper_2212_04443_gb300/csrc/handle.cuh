@@ -41,6 +41,7 @@ struct bchdav_handle_s {
   DevBuf lg_cnt, lg_off, lg_tiles, lg_row, lg_pseg;
   bchdav::SpmmLong lg;
   DevBuf gnn, gnn_opt, gnn_w;   // start-block network: activations, optimiser state, Ritz step
+  DevBuf km, km_x;              // clustering: centroids, sums, seeding state; transposed features
   const bchdav::SpmmLong* long_rows() const { return lg.n_seg > 0 ? &lg : nullptr; }
   std::vector<bchdav_iter_record> history;
   // filter SpMM schedules found by timing (block size of the row kernel per matrix and width)
@@ -115,7 +116,7 @@ struct bchdav_handle_s {
   void release_all() {
     DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
                      &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part, &tc_err,
-                     &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w};
+                     &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w, &km, &km_x};
     lg = bchdav::SpmmLong();
     for (DevBuf* b : all) b->release();
     for (bchdav_handle_s* w : workers) {

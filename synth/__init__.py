@@ -68,6 +68,25 @@ def kmeans_first(n: int, seed: int) -> int:
     return int(rng(seed).integers(0, n))
 
 
+def planted_embedding(n: int, c: int, dim: int, noise: float = 0.05, seed: int = 0,
+                      contiguous: bool = True):
+    """Block shaped like the k leading eigenvectors of a c-cluster graph: row i is
+    q_{label_i} / sqrt(n_{label_i}) plus isotropic Gaussian noise whose expected length is about
+    `noise` times that row's length, q_j orthonormal directions in R^dim (dim >= c).  Labels are cluster-contiguous (as the SBM
+    numbers its nodes) or shuffled.  Returns (V float64 n x dim, labels int32)."""
+    g = rng(seed)
+    sizes = np.full(c, n // c, dtype=np.int64)
+    sizes[: n % c] += 1
+    labels = np.repeat(np.arange(c, dtype=np.int32), sizes)
+    if not contiguous:
+        labels = labels[g.permutation(n)]
+    Q, _ = np.linalg.qr(g.standard_normal((dim, c)))
+    scale = 1.0 / np.sqrt(sizes[labels].astype(np.float64))
+    V = Q.T[labels] * scale[:, None]
+    V += g.standard_normal((n, dim)) * (noise / np.sqrt(dim) * scale)[:, None]
+    return V, labels
+
+
 def gnn_init(d_in: int, width: int, k: int, layers: int = 3, seed: int = 0) -> np.ndarray:
     """Flat float32 initial parameters of the start-block network: every weight matrix
     (fan_in x fan_out) normal with standard deviation sqrt(1 / fan_in), biases zero, in the
