@@ -445,7 +445,7 @@ def cluster_leg(H, g, evecs, stream, sm_max_mhz, with_oracle):
            "stages_agree": same,
            "row_normalize_gbs": round(n * k * 12 / t_norm / 1e9, 1),
            "seeding_gbs": round((c - 1) * n * (4 * k + 8) / t_seed / 1e9, 1),
-           "roofline": {"kernel": "km_assign_kernel (Lloyd rounds, whole bchdav_kmeans call)",
+           "roofline": {"kernel": "km_assign_all_kernel (Lloyd rounds, whole bchdav_kmeans call)",
                         "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
                         "unit": "Tops/s (float32)", "frac": round(ach / peak, 4),
                         "traffic": None,

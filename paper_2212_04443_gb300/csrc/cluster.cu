@@ -326,9 +326,10 @@ __global__ void __launch_bounds__(kKmThreads) km_assign_kernel(KmArgs a) {
 // zero centroids that are never chosen).  Warps run independently: each takes 64-node chunks
 // from a counter, two nodes per lane, so that one shared-memory load of a centroid pair feeds
 // both nodes; the features of the next four dimensions are loaded before the current four are
-// used.
+// used.  Up to 20 centroids per block the registers are capped for three CTAs per SM (24 warps;
+// the fastest of two and three CTAs measured at 1M nodes x 100 centroids x 100 dimensions).
 template <int CB, bool SMEM_SUM>
-__global__ void __launch_bounds__(kKmThreads) km_assign_all_kernel(KmArgs a) {
+__global__ void __launch_bounds__(kKmThreads, CB <= 20 ? 3 : 2) km_assign_all_kernel(KmArgs a) {
   static_assert(CB % 2 == 0, "centroids are processed in pairs");
   constexpr int CP = CB / 2;
   extern __shared__ __align__(16) unsigned char km_smem[];
