@@ -23,7 +23,9 @@ paper states:
 * ``gnn``        the learned start block (an extension feeding V_init): network,
                  subspace-alignment loss, its gradient, Adam, Ritz ordering;
 * ``cluster``    Algorithm 1, Steps 4-5: row normalisation of the eigenvectors and
-                 Lloyd's k-means on the rows; adjusted Rand index and NMI.
+                 Lloyd's k-means on the rows; adjusted Rand index and NMI;
+* ``lanczos``    spectrum bounds by k-step Lanczos for matrices without analytic bounds
+                 (Sec. 2), e.g. the combinatorial Laplacian D - S (``laplacian``, kind).
 
 Pins (tests/test_oracle_*.py, run with ``-m "not gpu"``): closed-form spectra
 of cycles, paths, hypercubes, complete and complete-bipartite graphs and their
@@ -41,3 +43,4 @@ from .dgks import dgks_orthonormalize  # noqa: F401
 from .bchdav import bchdav, BchdavResult, default_params, relative_residuals  # noqa: F401
 from . import gnn  # noqa: F401
 from . import cluster  # noqa: F401
+from . import lanczos  # noqa: F401

@@ -3,7 +3,7 @@
 Restated step by step in float64.  Readings of points the paper leaves open
 (each is applied identically by the CUDA path):
 
-* bounds: lowb = 0, upperb = 2 (normalized Laplacian, Sec. 2 and Sec. 4.1);
+* bounds: lowb = 0, upperb = 2 (normalized Laplacian, Sec. 2 and Sec. 4.1), or given (Lanczos);
   initial low_nwb = lowb + (upperb - lowb) * k_want / N.
 * defaults: act_max = max(5 k_b, 30), dim_max = max(act_max + 2 k_b, k + 30)
   (Sec. 4), k_ri = max(floor(act_max/2), act_max - 3 k_b), k_ro = dim_max -
@@ -82,8 +82,10 @@ def relative_residuals(A, evals, evecs) -> np.ndarray:
 def bchdav(A, k_want: int, b: int, m: int, act_max: int | None, tol: float, *,
            V_init: np.ndarray | None = None, dim_max: int | None = None, itmax: int = 1000,
            seed: int = 0, tau_dep: float = TAU_DEP_F64, record: bool = True,
-           max_iters_run: int | None = None) -> BchdavResult:
-    """k_want smallest eigenpairs of the symmetric operator A with spectrum in [0, 2].
+           max_iters_run: int | None = None, bounds: tuple | None = None) -> BchdavResult:
+    """k_want smallest eigenpairs of the symmetric operator A with spectrum in [0, 2], or in
+    [lowb, upperb] given as ``bounds`` (e.g. from oracle/lanczos.py for matrices whose bounds
+    are not analytic, Sec. 2).
 
     ``A`` is a scipy sparse matrix (or anything with ``@`` and ``shape``).
     ``max_iters_run`` stops early (for bounded timing samples) without error.
@@ -99,7 +101,9 @@ def bchdav(A, k_want: int, b: int, m: int, act_max: int | None, tol: float, *,
         raise ValueError("subspace larger than the problem")
 
     # Step 1: bounds.
-    lowb, upperb = LOWB, UPPERB
+    lowb, upperb = (LOWB, UPPERB) if bounds is None else (float(bounds[0]), float(bounds[1]))
+    if not upperb > lowb:
+        raise ValueError("bounds: need lowb < upperb")
     low_nwb = lowb + (upperb - lowb) * k_want / N
 
     # Step 2: first filter input.
