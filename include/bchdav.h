@@ -64,6 +64,14 @@ typedef struct {
   const float* val_f32;    /* nnz or NULL */
 } bchdav_csr;
 
+/* Step 1 of Algorithm 2: the spectrum bounds of the filter (Sec. 2).  The first low_nwb is
+ * lowb + (upperb - lowb) k / N in every mode. */
+typedef enum {
+  BCHDAV_BOUNDS_NORMALIZED = 0,  /* lowb = 0, upperb = 2: the normalized Laplacian (Eq. (1)) */
+  BCHDAV_BOUNDS_GIVEN = 1,       /* opts.lowb, opts.upperb */
+  BCHDAV_BOUNDS_LANCZOS = 2      /* k-step Lanczos estimate (bchdav_lanczos_bounds), seed = opts.seed */
+} bchdav_bounds;
+
 /* Optional parameters of bchdav_solve; zero-initialise for the defaults. */
 typedef struct {
   int32_t dim_max;          /* 0: min(max(act_max + 2b, k + 30), N)  (Sec. 4 defaults) */
@@ -78,7 +86,10 @@ typedef struct {
   int32_t k_init;
   int32_t ld_v_init;
   int32_t record_history;   /* nonzero: keep per-iteration counters (bchdav_history) */
-  int32_t reserved1;
+  int32_t bounds;           /* bchdav_bounds: where Step 1's lowb and upperb come from */
+  double lowb, upperb;      /* BCHDAV_BOUNDS_GIVEN: the bounds (lowb < upperb) */
+  int32_t lanczos_steps;    /* BCHDAV_BOUNDS_LANCZOS: steps of the estimate (0: 20; <= 64) */
+  int32_t reserved3;
 } bchdav_opts;
 
 /* Results and per-component device time of one solve. */
@@ -95,6 +106,7 @@ typedef struct {
   int64_t n_kernel_launches;/* kernels this library launched during the solve */
   int32_t status;           /* the solve's return status (set by bchdav_solve_batched) */
   int32_t reserved2;
+  double lowb, upperb;      /* the bounds Step 1 used */
 } bchdav_info;
 
 /* One record per outer iteration when opts.record_history is set. */
@@ -129,6 +141,21 @@ bchdav_status bchdav_build_laplacian(bchdav_handle h, int32_t n, int64_t n_edges
                                      const int32_t* src, const int32_t* dst, bchdav_csr* out);
 bchdav_status bchdav_free_csr(bchdav_handle h, bchdav_csr* csr);
 
+/* The graph matrices the library assembles.  The combinatorial Laplacian L = D - S has the
+ * same pattern as Eq. (1), off-diagonal -1.0 and diagonal d_i (0.0 for an isolated node); its
+ * spectrum lies in [0, 2 max d_i], and its bounds for Algorithm 2 come from
+ * BCHDAV_BOUNDS_LANCZOS or BCHDAV_BOUNDS_GIVEN. */
+typedef enum {
+  BCHDAV_LAPLACIAN_NORMALIZED = 0,     /* Eq. (1) */
+  BCHDAV_LAPLACIAN_COMBINATORIAL = 1   /* D - S */
+} bchdav_laplacian_kind;
+
+/* bchdav_build_laplacian for the matrix of the given kind (same arguments, layout, ownership
+ * and errors; an unknown kind gives BCHDAV_ERR_ARG). */
+bchdav_status bchdav_build_laplacian_kind(bchdav_handle h, int32_t n, int64_t n_edges,
+                                          const int32_t* src, const int32_t* dst, int32_t kind,
+                                          bchdav_csr* out);
+
 /* Copy the arrays of csr into caller-owned device arrays (n + 1 and nnz
  * entries; val_f32 may be NULL to skip it), ordered on the handle's stream and
  * complete when the call returns. */
@@ -138,6 +165,21 @@ bchdav_status bchdav_copy_csr(bchdav_handle h, const bchdav_csr* csr, int32_t* r
 /* Check a caller-built CSR on the device (row pointers monotone, columns in
  * range and strictly ascending per row).  BCHDAV_ERR_CSR when it is not. */
 bchdav_status bchdav_check_csr(bchdav_handle h, const bchdav_csr* A);
+
+/* ---- Sec. 2: spectrum bounds when they are not analytic -------------------- */
+
+/* k-step Lanczos estimate of the bounds of the symmetric matrix A (any CSR: both triangles
+ * stored).  Start vector v_1 = u/||u||, u_i uniform in [-1/2, 1/2) from Philox4x32-10 stream 3,
+ * vector 0, the given seed; steps w = A v_j - beta_{j-1} v_{j-1}, alpha_j = v_j . w,
+ * w -= alpha_j v_j, beta_j = ||w||, v_{j+1} = w / beta_j, no reorthogonalisation; an exactly
+ * zero beta_j ends it after step j.  With theta the eigenvalues of the tridiagonal T:
+ * *lowb = theta_min and *upperb = theta_max + beta_last (the residual norm of the Lanczos
+ * relation; Zhou and Li's estimator).  lowb, upperb, alpha, beta (steps doubles each, may be
+ * NULL) and steps_done (may be NULL) are HOST pointers.  1 <= steps <= min(64, N), else
+ * BCHDAV_ERR_ARG.  Synchronises the handle's stream. */
+bchdav_status bchdav_lanczos_bounds(bchdav_handle h, const bchdav_csr* A, int32_t steps,
+                                    uint64_t seed, double* lowb, double* upperb, double* alpha,
+                                    double* beta, int32_t* steps_done);
 
 /* ---- Algorithm 2 ---------------------------------------------------------- */
 

@@ -15,7 +15,8 @@ from dataclasses import dataclass
 
 __all__ = [
     "lib", "build", "Handle", "DeviceCSR", "BchdavError", "SolveInfo", "IterRecord",
-    "PREC_FP64", "PREC_MIXED", "EXPORTED_SYMBOLS", "launch_count",
+    "PREC_FP64", "PREC_MIXED", "EXPORTED_SYMBOLS", "launch_count", "LAPLACIAN_NORMALIZED",
+    "LAPLACIAN_COMBINATORIAL", "BOUNDS_NORMALIZED", "BOUNDS_GIVEN", "BOUNDS_LANCZOS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -23,6 +24,9 @@ _LIB_PATH = os.path.join(_HERE, "_lib", "libbchdav.so")
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+LAPLACIAN_NORMALIZED = 0      # Eq. (1)
+LAPLACIAN_COMBINATORIAL = 1   # D - S
+BOUNDS_NORMALIZED, BOUNDS_GIVEN, BOUNDS_LANCZOS = 0, 1, 2
 
 STATUS = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "invalid CSR",
           -3: "out of device memory", -4: "CUDA error", -5: "non-finite value",
@@ -37,6 +41,7 @@ EXPORTED_SYMBOLS = [
     "bchdav_launch_count", "bchdav_gnn_n_params", "bchdav_gnn_forward", "bchdav_gnn_loss_grad",
     "bchdav_gnn_train", "bchdav_gnn_start_block", "bchdav_release_workspace",
     "bchdav_row_normalize", "bchdav_kmeans_seed", "bchdav_kmeans", "bchdav_spectral_cluster",
+    "bchdav_build_laplacian_kind", "bchdav_lanczos_bounds",
 ]
 
 
@@ -60,7 +65,8 @@ class OptsStruct(C.Structure):
     _fields_ = [("dim_max", C.c_int32), ("itmax", C.c_int32), ("precision", C.c_int32),
                 ("dense_path", C.c_int32), ("seed", C.c_uint64), ("v_init", C.c_void_p),
                 ("k_init", C.c_int32), ("ld_v_init", C.c_int32), ("record_history", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("bounds", C.c_int32), ("lowb", C.c_double), ("upperb", C.c_double),
+                ("lanczos_steps", C.c_int32), ("reserved3", C.c_int32)]
 
 
 class InfoStruct(C.Structure):
@@ -70,7 +76,8 @@ class InfoStruct(C.Structure):
                 ("ms_spmm_w", C.c_double), ("ms_h", C.c_double), ("ms_eig", C.c_double),
                 ("ms_rot", C.c_double), ("ms_resid", C.c_double), ("ms_other", C.c_double),
                 ("filter_bytes", C.c_double), ("filter_ms_kernels", C.c_double),
-                ("n_kernel_launches", C.c_int64), ("status", C.c_int32), ("reserved2", C.c_int32)]
+                ("n_kernel_launches", C.c_int64), ("status", C.c_int32), ("reserved2", C.c_int32),
+                ("lowb", C.c_double), ("upperb", C.c_double)]
 
 
 class IterStruct(C.Structure):
@@ -135,6 +142,9 @@ def lib() -> C.CDLL:
         "bchdav_gram": (i32, [p, i32, p, i32, i32, p, i32, i32, p, i32]),
         "bchdav_eigh_noalloc": (i32, [i32, p, i32, p, p, i32, p]),
         "bchdav_row_normalize": (i32, [p, i32, i32, p, i64, p, i64]),
+        "bchdav_build_laplacian_kind": (i32, [p, i32, i64, p, p, i32, C.POINTER(CSRStruct)]),
+        "bchdav_lanczos_bounds": (i32, [p, C.POINTER(CSRStruct), i32, u64, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), p, p, C.POINTER(C.c_int32)]),
         "bchdav_kmeans_seed": (i32, [p, i32, i32, p, i64, i32, i32, p]),
         "bchdav_kmeans": (i32, [p, i32, i32, p, i64, i32, p, i32, p, p, C.POINTER(C.c_int32)]),
         "bchdav_spectral_cluster": (i32, [p, i32, i32, p, i64, i32, i32, i32, p, p, p,
@@ -146,6 +156,19 @@ def lib() -> C.CDLL:
         fn.argtypes = args
     _lib = L
     return L
+
+
+def _set_bounds(opts, bounds, lanczos_steps):
+    if bounds is None:
+        opts.bounds = BOUNDS_NORMALIZED
+    elif isinstance(bounds, str):
+        if bounds != "lanczos":
+            raise ValueError(f"bounds: {bounds!r}")
+        opts.bounds = BOUNDS_LANCZOS
+        opts.lanczos_steps = lanczos_steps
+    else:
+        opts.bounds = BOUNDS_GIVEN
+        opts.lowb, opts.upperb = float(bounds[0]), float(bounds[1])
 
 
 def _ptr(t) -> int:
@@ -182,6 +205,8 @@ class SolveInfo:
     filter_bytes: float
     filter_ms: float
     launches: int
+    lowb: float = 0.0
+    upperb: float = 2.0
 
 
 @dataclass
@@ -234,12 +259,13 @@ class Handle:
         self._check(self.L.bchdav_set_stream(self.h, C.c_void_p(self._stream)))
 
     # ---- Eq. (1)
-    def build_laplacian(self, n: int, src, dst) -> DeviceCSR:
-        """A = I - D^{-1/2} S D^{-1/2} from int32 CUDA edge tensors (library-built CSR)."""
+    def build_laplacian(self, n: int, src, dst, kind: int = LAPLACIAN_NORMALIZED) -> DeviceCSR:
+        """A = I - D^{-1/2} S D^{-1/2} (or with kind=LAPLACIAN_COMBINATORIAL, D - S) from int32
+        CUDA edge tensors (library-built CSR)."""
         import torch
         cs = CSRStruct()
-        self._check(self.L.bchdav_build_laplacian(self.h, n, int(src.numel()), _ptr(src), _ptr(dst),
-                                                  C.byref(cs)))
+        self._check(self.L.bchdav_build_laplacian_kind(self.h, n, int(src.numel()), _ptr(src),
+                                                       _ptr(dst), kind, C.byref(cs)))
         nnz = int(cs.nnz)
         dev = src.device
         # copy into torch-owned tensors, then release the library's arrays
@@ -263,7 +289,8 @@ class Handle:
     def solve(self, A: DeviceCSR, k: int, b: int, m: int, act_max: int, tol: float, *,
               v_init=None, precision: int = PREC_FP64, dim_max: int = 0, itmax: int = 0,
               seed: int = 0, record_history: bool = False, evals=None, evecs=None,
-              dense_path: int = 0):
+              dense_path: int = 0, bounds=None, lanczos_steps: int = 0):
+        """bounds: None (the normalized Laplacian's [0, 2]), (lowb, upperb), or "lanczos"."""
         import torch
         dev = A.rowptr.device
         if evals is None:
@@ -277,6 +304,7 @@ class Handle:
         opts.seed = seed
         opts.dense_path = dense_path
         opts.record_history = 1 if record_history else 0
+        _set_bounds(opts, bounds, lanczos_steps)
         if v_init is not None:
             assert v_init.dtype == torch.float64 and v_init.is_cuda and v_init.stride(1) == 1
             opts.v_init = _ptr(v_init)
@@ -290,7 +318,7 @@ class Handle:
         return evals, evecs, self._info(st, info)
 
     def solve_host(self, n, rowptr, colidx, val, k, b, m, act_max, tol, *, precision=PREC_FP64,
-                   seed=0, evals=None, evecs=None, v_init=None):
+                   seed=0, evals=None, evecs=None, v_init=None, bounds=None, lanczos_steps=0):
         """End-to-end call with host (numpy) arrays: copies in, solves, copies out."""
         import numpy as np
         if evals is None:
@@ -300,6 +328,7 @@ class Handle:
         opts = OptsStruct()
         opts.precision = precision
         opts.seed = seed
+        _set_bounds(opts, bounds, lanczos_steps)
         if v_init is not None:
             v_init = np.ascontiguousarray(v_init, dtype=np.float64)
             opts.v_init = v_init.ctypes.data
@@ -401,6 +430,19 @@ class Handle:
                                                   _ptr(ritz)))
         return V0, ritz
 
+    # ---- Sec. 2: spectrum bounds by k-step Lanczos
+    def lanczos_bounds(self, A: DeviceCSR, steps: int = 20, seed: int = 0):
+        """(lowb, upperb, alpha, beta) of the k-step estimate (numpy arrays of the steps done)."""
+        import numpy as np
+        lo, hi = C.c_double(0.0), C.c_double(0.0)
+        alpha, beta = np.zeros(steps), np.zeros(steps)
+        done = C.c_int32(0)
+        cs = A.struct()
+        self._check(self.L.bchdav_lanczos_bounds(self.h, C.byref(cs), steps, seed, C.byref(lo),
+                                                 C.byref(hi), alpha.ctypes.data,
+                                                 beta.ctypes.data, C.byref(done)))
+        return lo.value, hi.value, alpha[:done.value].copy(), beta[:done.value].copy()
+
     # ---- Algorithm 1, Steps 4-5: spectral clustering
     def row_normalize(self, V, Xt=None):
         """Transposed float32 features (dim x n) of the float64 row-major block V (n x dim)."""
@@ -462,7 +504,7 @@ class Handle:
                   resid=info.ms_resid, other=info.ms_other)
         return SolveInfo(st, info.iters, info.n_converged, info.n_spmm, info.n_replaced,
                          info.max_rel_resid, ms, info.filter_bytes, info.filter_ms_kernels,
-                         info.n_kernel_launches)
+                         info.n_kernel_launches, info.lowb, info.upperb)
 
     def history(self):
         n = self.L.bchdav_history(self.h, None, 0)

@@ -81,5 +81,6 @@ inline void note_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAX
 
 constexpr uint32_t kStreamReplace = 1;
 constexpr uint32_t kStreamFill = 2;
+constexpr uint32_t kStreamLanczos = 3;   // start vector of the Lanczos bound estimate
 
 }  // namespace bchdav

@@ -42,6 +42,7 @@ struct bchdav_handle_s {
   bchdav::SpmmLong lg;
   DevBuf gnn, gnn_opt, gnn_w;   // start-block network: activations, optimiser state, Ritz step
   DevBuf km, km_x;              // clustering: centroids, sums, seeding state; transposed features
+  DevBuf lz;                    // Lanczos bound estimate: three vectors, coefficients, T_k
   const bchdav::SpmmLong* long_rows() const { return lg.n_seg > 0 ? &lg : nullptr; }
   std::vector<bchdav_iter_record> history;
   // filter SpMM schedules found by timing (block size of the row kernel per matrix and width)
@@ -116,7 +117,7 @@ struct bchdav_handle_s {
   void release_all() {
     DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
                      &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part, &tc_err,
-                     &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w, &km, &km_x};
+                     &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w, &km, &km_x, &lz};
     lg = bchdav::SpmmLong();
     for (DevBuf* b : all) b->release();
     for (bchdav_handle_s* w : workers) {
@@ -138,3 +139,12 @@ struct bchdav_handle_s {
 // Long-row schedule of A (rows with more than kLongRow nonzeros become segments) with segment
 // workspace for products up to width_bytes per row (solver.cu); one host synchronisation.
 bchdav_status prepare_long_rows(bchdav_handle h, const bchdav_csr* A, size_t width_bytes);
+
+namespace bchdav {
+// k-step Lanczos bound estimate of the spectrum of A (lanczos.cu): lowb = theta_min,
+// upperb = theta_max + beta_k; alpha/beta (host, may be NULL) receive the coefficients of the
+// steps done (fewer than `steps` when some beta_j is exactly 0).
+bchdav_status lanczos_bounds(bchdav_handle h, const bchdav_csr* A, int steps,
+                             unsigned long long seed, double* lowb, double* upperb,
+                             double* alpha_out, double* beta_out, int* steps_done);
+}  // namespace bchdav

@@ -260,18 +260,23 @@ __global__ void long_count_kernel(int nl, const int* __restrict__ rows, const lo
   }
 }
 
-__global__ void rsqrt_deg_kernel(int n, const int* __restrict__ deg, double* __restrict__ r) {
+// r_i = 1/sqrt(d_i) (0 for an isolated node) for Eq. (1); d_i itself for L = D - S
+__global__ void rsqrt_deg_kernel(int n, const int* __restrict__ deg, double* __restrict__ r,
+                                 int kind) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int d = deg[i];
-    r[i] = d > 0 ? 1.0 / sqrt((double)d) : 0.0;
+    r[i] = kind == BCHDAV_LAPLACIAN_COMBINATORIAL ? (double)d
+                                                  : (d > 0 ? 1.0 / sqrt((double)d) : 0.0);
   }
 }
 
-// One warp per row: distinct neighbours plus the diagonal, ascending.
+// One warp per row: distinct neighbours plus the diagonal, ascending.  Eq. (1): off-diagonal
+// -(r_i r_j), diagonal 1; L = D - S: off-diagonal -1, diagonal d_i (r_i holds d_i).
 __global__ void fill_kernel(int n, const long long* __restrict__ start, const int* __restrict__ adj,
                             const long long* __restrict__ rowptr64, const double* __restrict__ r,
                             int* __restrict__ rowptr, int* __restrict__ colidx,
-                            double* __restrict__ val, float* __restrict__ val32) {
+                            double* __restrict__ val, float* __restrict__ val32, int kind) {
+  const bool comb = kind == BCHDAV_LAPLACIAN_COMBINATORIAL;
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += warps) {
@@ -298,7 +303,7 @@ __global__ void fill_kernel(int n, const long long* __restrict__ start, const in
       if (uniq) {
         int rank = written + __popc(m & ((1u << lane) - 1u));
         long long pos = o0 + rank + (v > row ? 1 : 0);
-        double x = -(ri * r[v]);
+        double x = comb ? -1.0 : -(ri * r[v]);
         colidx[pos] = v;
         val[pos] = x;
         val32[pos] = __double2float_rn(x);
@@ -309,8 +314,8 @@ __global__ void fill_kernel(int n, const long long* __restrict__ start, const in
     if (lane == 0) {
       long long pos = o0 + below;
       colidx[pos] = row;
-      val[pos] = 1.0;
-      val32[pos] = 1.0f;
+      val[pos] = comb ? ri : 1.0;
+      val32[pos] = comb ? __double2float_rn(ri) : 1.0f;
     }
   }
 }
@@ -406,9 +411,16 @@ extern "C" bchdav_status bchdav_copy_csr(bchdav_handle h, const bchdav_csr* csr,
 extern "C" bchdav_status bchdav_build_laplacian(bchdav_handle h, int32_t n, int64_t n_edges,
                                                 const int32_t* src, const int32_t* dst,
                                                 bchdav_csr* out) {
+  return bchdav_build_laplacian_kind(h, n, n_edges, src, dst, BCHDAV_LAPLACIAN_NORMALIZED, out);
+}
+
+extern "C" bchdav_status bchdav_build_laplacian_kind(bchdav_handle h, int32_t n, int64_t n_edges,
+                                                     const int32_t* src, const int32_t* dst,
+                                                     int32_t kind, bchdav_csr* out) {
   if (!h) return BCHDAV_ERR_ARG;
   if (n < 1 || n_edges < 0 || (n_edges > 0 && (!src || !dst)) || !out ||
-      2 * n_edges + n >= (int64_t)INT32_MAX) {
+      2 * n_edges + n >= (int64_t)INT32_MAX ||
+      (kind != BCHDAV_LAPLACIAN_NORMALIZED && kind != BCHDAV_LAPLACIAN_COMBINATORIAL)) {
     h->set_error(BCHDAV_ERR_ARG, "build_laplacian: invalid arguments");
     return BCHDAV_ERR_ARG;
   }
@@ -511,7 +523,7 @@ extern "C" bchdav_status bchdav_build_laplacian(bchdav_handle h, int32_t n, int6
   HCUDA(exclusive_scan(st, n, deg, 1, rp64, tiles));
   long long nnz = 0;
   HCUDA(cudaMemcpyAsync(&nnz, rp64 + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
-  rsqrt_deg_kernel<<<grid_for(n), 256, 0, st>>>(n, deg, r); note_launch();
+  rsqrt_deg_kernel<<<grid_for(n), 256, 0, st>>>(n, deg, r, kind); note_launch();
   HCUDA(cudaGetLastError());
   HCUDA(cudaStreamSynchronize(st));
   int32_t* rowptr = nullptr;
@@ -531,7 +543,7 @@ extern "C" bchdav_status bchdav_build_laplacian(bchdav_handle h, int32_t n, int6
     return BCHDAV_ERR_OOM;
   }
   fill_kernel<<<grid_for((long long)n * 32), 256, 0, st>>>(n, start, adj, rp64, r, rowptr, colidx,
-                                                          val, val32); note_launch();
+                                                          val, val32, kind); note_launch();
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {

@@ -690,7 +690,12 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   if (k < 1 || k > N || b < 1 || b > 64 || m < 1 || act_max < 2 * b || act_max > N ||
       !(tol > 0) || !evals || !evecs || (prec != BCHDAV_PREC_FP64 && prec != BCHDAV_PREC_MIXED) ||
       (opts.k_init > 0 && (!opts.v_init || opts.ld_v_init < opts.k_init)) ||
-      opts.dense_path < 0 || opts.dense_path > 2) {
+      opts.dense_path < 0 || opts.dense_path > 2 || opts.bounds < BCHDAV_BOUNDS_NORMALIZED ||
+      opts.bounds > BCHDAV_BOUNDS_LANCZOS ||
+      (opts.bounds == BCHDAV_BOUNDS_GIVEN &&
+       !(std::isfinite(opts.lowb) && std::isfinite(opts.upperb) && opts.lowb < opts.upperb)) ||
+      (opts.bounds == BCHDAV_BOUNDS_LANCZOS &&
+       (opts.lanczos_steps < 0 || opts.lanczos_steps > 64 || opts.lanczos_steps > N))) {
     h->set_error(BCHDAV_ERR_ARG, "solve: invalid k, b, m, act_max, tol or options");
     return BCHDAV_ERR_ARG;
   }
@@ -789,8 +794,21 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   const unsigned long long launches0 = __atomic_load_n(&bchdav::g_launches, __ATOMIC_RELAXED);
   tm_total.start(st);
 
-  // ---- Step 1: bounds
-  const double lowb = 0.0, upperb = 2.0;
+  // ---- Step 1: bounds (analytic for Eq. (1), given, or by k-step Lanczos)
+  double lowb = 0.0, upperb = 2.0;
+  if (opts.bounds == BCHDAV_BOUNDS_GIVEN) {
+    lowb = opts.lowb;
+    upperb = opts.upperb;
+  } else if (opts.bounds == BCHDAV_BOUNDS_LANCZOS) {
+    const int steps = opts.lanczos_steps > 0 ? opts.lanczos_steps : std::min(20, N);
+    BCHDAV_TRY(bchdav::lanczos_bounds(h, A, steps, opts.seed, &lowb, &upperb, nullptr, nullptr,
+                                      nullptr));
+    if (!(upperb > lowb)) {
+      h->set_error(BCHDAV_ERR_ARG, "solve: the Lanczos estimate gives lowb >= upperb "
+                                   "(a multiple of the identity?)");
+      return BCHDAV_ERR_ARG;
+    }
+  }
   double low_nwb = lowb + (upperb - lowb) * (double)k / (double)N;
 
   // ---- Step 2: first filter input
@@ -1092,6 +1110,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     info->filter_ms_kernels = tm_filter.acc;
     info->n_kernel_launches =
         (int64_t)(__atomic_load_n(&bchdav::g_launches, __ATOMIC_RELAXED) - launches0);
+    info->lowb = lowb;
+    info->upperb = upperb;
   }
   return converged ? BCHDAV_OK : BCHDAV_NOT_CONVERGED;
 }
