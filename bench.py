@@ -205,7 +205,10 @@ def run_ours(args):
     H = P.Handle()
     src = torch.from_numpy(g.src).cuda()
     dst = torch.from_numpy(g.dst).cuda()
-    A = H.build_laplacian(g.n, src, dst)
+    kind = P.LAPLACIAN_COMBINATORIAL if w.get("kind") == "combinatorial" else \
+        P.LAPLACIAN_NORMALIZED
+    A = H.build_laplacian(g.n, src, dst, kind=kind)
+    bounds, lz_steps = w.get("bounds"), w.get("lanczos_steps", 0)
     V0 = torch.from_numpy(synth.gaussian_block(g.n, b, w["v0_seed"])).cuda()
     evals = torch.zeros(k, dtype=torch.float64, device="cuda")
     evecs = torch.zeros((g.n, k), dtype=torch.float64, device="cuda")
@@ -216,7 +219,7 @@ def run_ours(args):
     def solve(precision, record=True):
         return H.solve(A, k, b, m, act, tol, v_init=V0, precision=precision,
                        record_history=record, evals=evals, evecs=evecs, itmax=200,
-                       dense_path=dense_path)
+                       dense_path=dense_path, bounds=bounds, lanczos_steps=lz_steps)
 
     for _ in range(args.warmup):
         solve(prec)
@@ -329,13 +332,27 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             H.solve_host(n, rpn, cin, van, k, b, m, act, tol, precision=prec, v_init=v0n,
-                         evals=evh.numpy(), evecs=evech.numpy())
+                         evals=evh.numpy(), evecs=evech.numpy(), bounds=bounds,
+                         lanczos_steps=lz_steps)
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
         h2d = rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8 + v0h.numel() * 8
         d2h = k * 8 + n * k * 8
         out["e2e"] = {"value": round(min(e2e_times), 4), "unit": "s",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    # ---- Step 1 bounds (Sec. 2): the k-step Lanczos estimate timed alone
+    if bounds == "lanczos" and rank == 0:
+        steps = lz_steps or 20
+        H.lanczos_bounds(A, steps, 0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lo, hi, _, _ = H.lanczos_bounds(A, steps, 0)
+        e1.record(stream)
+        e1.synchronize()
+        t_lz = e0.elapsed_time(e1) / 1e3
+        out["bounds"] = {"mode": "lanczos", "steps": steps, "lowb": lo, "upperb": hi,
+                         "seconds": round(t_lz, 5), "in_solve": [info.lowb, info.upperb]}
     # ---- Algorithm 1, Steps 4-5 on the eigenvectors (graphs with planted labels)
     if not args.no_cluster and rank == 0 and g.labels is not None:
         try:
@@ -522,6 +539,19 @@ def warm_start_leg(H, A, g, k, b, m, act, tol, prec, stream, evals, evecs):
                        for r in rnd]}
 
 
+def oracle_problem(w):
+    """The workload's matrix as the oracle builds it, and its Step 1 bounds (None: [0, 2])."""
+    import oracle
+    from oracle import lanczos
+    g = w["graph"]
+    Asp = oracle.laplacian_csr(g.n, g.src, g.dst, kind=w.get("kind", "normalized")).scipy()
+    bnd = None
+    if w.get("bounds") == "lanczos":
+        lo, hi, _, _ = lanczos.bounds(Asp, w.get("lanczos_steps") or 20, 0)
+        bnd = (lo, hi)
+    return Asp, bnd
+
+
 def cpu_baseline(workload, gpu_iters, n_iter=2):
     """The oracle as it stands, timed on this host: the first n_iter outer iterations of the
     same solve, scaled by the iteration count of the full solve."""
@@ -529,12 +559,11 @@ def cpu_baseline(workload, gpu_iters, n_iter=2):
     import synth
     w = synth.workload(workload)
     g = w["graph"]
-    L = oracle.laplacian_csr(g.n, g.src, g.dst)
-    Asp = L.scipy()
+    Asp, bnd = oracle_problem(w)
     V0 = synth.gaussian_block(g.n, w["b"], w["v0_seed"])
     t0 = time.perf_counter()
     oracle.bchdav(Asp, w["k"], w["b"], w["m"], w["act_max"], w["tol"], V_init=V0,
-                  max_iters_run=n_iter, record=False)
+                  max_iters_run=n_iter, record=False, bounds=bnd)
     dt = time.perf_counter() - t0
     per_it = dt / n_iter
     golden = os.path.join(ROOT, "tests", "golden", f"oracle_{workload}.json")
@@ -558,8 +587,7 @@ def run_reference(args):
     import synth
     w = synth.workload(args.workload)
     g = w["graph"]
-    L = oracle.laplacian_csr(g.n, g.src, g.dst)
-    Asp = L.scipy()
+    Asp, bnd = oracle_problem(w)
     V0 = synth.gaussian_block(g.n, w["b"], w["v0_seed"])
     golden = os.path.join(ROOT, "tests", "golden", f"oracle_{args.workload}.json")
     iters = None
@@ -570,7 +598,7 @@ def run_reference(args):
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         oracle.bchdav(Asp, w["k"], w["b"], w["m"], w["act_max"], w["tol"], V_init=V0,
-                      max_iters_run=1, record=False)
+                      max_iters_run=1, record=False, bounds=bnd)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             per.append(dt)

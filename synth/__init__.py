@@ -376,6 +376,7 @@ def workload(name: str) -> dict:
 
     sbm10k   : SBM N=10,000, 10 clusters, p_in=1e-3, p_out=2e-5, k=10, b=5, m=11, act_max=30
     sbm1m    : SBM N=1,000,000, 100 clusters, d_in=16, d_out=2, k=100, b=20, m=15, act_max=300
+    sbm1m_comb: the same graph's combinatorial Laplacian D - S, bounds by 20-step Lanczos
     knn2m    : kNN-GMM 2,000,000 x 16-D, 50 components, 10-NN, k=50, b=10, m=13, act_max=150
     rmat24   : R-MAT scale 24, ef 16, k=64, b=16, m=15, act_max=192
     Scaled-down variants (for tests) take a suffix, e.g. ``sbm1m@50000`` keeps
@@ -388,10 +389,15 @@ def workload(name: str) -> dict:
         gr = sbm_edges(n, 10, p_in=1e-3 * 10000 / n, p_out=2e-5 * 10000 / n, seed=1)
         return dict(graph=gr, k=10, b=5, m=11, act_max=30, tol=tol, v0_seed=0,
                     desc=f"SBM N={n} c=10 p_in=1e-3 p_out=2e-5")
-    if base == "sbm1m":
+    if base in ("sbm1m", "sbm1m_comb"):
         n = int(size) if size else 1000000
         c = 100 if n >= 100000 else max(4, n // 10000)
         gr = sbm_edges(n, c, d_in=16.0, d_out=2.0, seed=2)
+        if base == "sbm1m_comb":
+            return dict(graph=gr, k=c, b=20, m=15, act_max=300, tol=tol, v0_seed=0,
+                        kind="combinatorial", bounds="lanczos", lanczos_steps=20,
+                        desc=f"combinatorial Laplacian D - S of the SBM N={n} c={c} d_in=16 "
+                             f"d_out=2, bounds by 20-step Lanczos")
         return dict(graph=gr, k=c, b=20, m=15, act_max=300, tol=tol, v0_seed=0,
                     desc=f"SBM N={n} c={c} d_in=16 d_out=2")
     if base == "knn2m":
