@@ -308,6 +308,93 @@ def knn_gmm_edges(n: int, dim: int = 16, n_comp: int = 50, knn: int = 10, seed: 
     return _as_graph(n, src[keep], dst[keep], f"knn{n}", comp.astype(np.int32))
 
 
+def powerlaw_tree_edges(n: int, avg_deg: float = 3.0, seed: int = 9) -> Graph:
+    """Ultra-sparse power-law graph with giant hubs, connected (stand-in for the MAWI traffic
+    graph of Table 2: N = 18M, average degree 3.0, heavy row imbalance).
+
+    Node weights w_j = 1/(j + 1) (Zipf).  A random recursive tree: node i >= 1 joins one
+    earlier node j < i drawn with probability w_j / sum_{l<i} w_l; then Chung-Lu edges, both
+    endpoints drawn with probability proportional to w, self loops and repeats removed, in up
+    to four rounds until the graph has n * avg_deg / 2 edges.  Node ids are permuted uniformly
+    at random at the end.
+    Most nodes end with degree 1 (leaves of hubs); the largest hub holds about n / ln n."""
+    g = rng(seed)
+    w = 1.0 / (np.arange(n, dtype=np.float64) + 1.0)
+    C = np.cumsum(w)
+    i = np.arange(1, n, dtype=np.int64)
+    parent = np.minimum(np.searchsorted(C, g.random(n - 1) * C[i - 1], side="right"), i - 1)
+    target = int(round(n * avg_deg / 2))
+    keys = _unique_pairs(i, parent, n)
+    for _ in range(4):                       # Chung-Lu edges until the target count is met
+        m_extra = target - keys.size
+        if m_extra <= 0:
+            break
+        q = np.sort(g.random(2 * m_extra)) * C[-1]      # sorted queries: cache-friendly search
+        ends = np.minimum(np.searchsorted(C, q, side="right"), n - 1)
+        ends = ends[g.permutation(ends.size)]
+        u, v = ends[:m_extra], ends[m_extra:]
+        keep = u != v
+        keys = _sorted_unique(np.concatenate([keys, _unique_pairs(u[keep], v[keep], n)]))
+    perm = g.permutation(n).astype(np.int64)
+    return _as_graph(n, perm[keys // n], perm[keys % n], f"powerlaw{n}")
+
+
+def dcsbm_edges(n: int, c: int, avg_deg: float, between: float, size_var: str = "low",
+                seed: int = 10) -> Graph:
+    """Degree-corrected SBM with block overlap and block size variation (stand-in for the
+    HPEC Graph Challenge partition graphs of Sec. 4.1, LBO/HBO x LBSV/HBSV; Table 2 lists
+    5M- and 20M-node ones with average degree 48.5).
+
+    Block sizes: n times Dirichlet(200) proportions ("low" variation) or Dirichlet(1) ("high");
+    node ids block-contiguous (labels = block).  Degree weights theta_i: Pareto with tail
+    exponent 2.5, capped at 10.  Each edge draw: first endpoint u with probability proportional
+    to theta; with probability 1 - `between` the second endpoint v proportional to theta inside
+    u's block, else proportional to theta outside it.  Drawn as multinomial counts per node (the
+    same distribution as independent draws, in O(n + m)): first endpoints per node, second
+    endpoints per block, paired by a random permutation; outside-block endpoints drawn over all
+    nodes and redrawn while in u's block.  Self loops and repeats are removed and more edges
+    drawn, in up to four rounds, until the graph has n * avg_deg / 2 edges."""
+    g = rng(seed)
+    alpha = 200.0 if size_var == "low" else 1.0
+    sizes = np.maximum(1, np.round(g.dirichlet(np.full(c, alpha)) * n)).astype(np.int64)
+    sizes[int(np.argmax(sizes))] += n - int(sizes.sum())
+    labels = np.repeat(np.arange(c, dtype=np.int32), sizes)
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    theta = np.minimum((1.0 - g.random(n)) ** (-1.0 / 1.5), 10.0)
+    p_all = theta / theta.sum()
+
+    def draw(m):
+        u = np.repeat(np.arange(n, dtype=np.int64), g.multinomial(m, p_all))
+        bu = labels[u]
+        within = g.random(m) >= between
+        v = np.empty(m, dtype=np.int64)
+        e_start = np.searchsorted(bu, np.arange(c + 1))   # u is sorted, so by block
+        for b in range(c):
+            idx = e_start[b] + np.flatnonzero(within[e_start[b]:e_start[b + 1]])
+            if idx.size == 0:
+                continue
+            s0, s1 = int(starts[b]), int(starts[b + 1])
+            tb = theta[s0:s1]
+            cnt = g.multinomial(idx.size, tb / tb.sum())
+            v[idx] = np.repeat(np.arange(s0, s1, dtype=np.int64), cnt)[g.permutation(idx.size)]
+        idx = np.flatnonzero(~within)
+        while idx.size:
+            vv = np.repeat(np.arange(n, dtype=np.int64), g.multinomial(idx.size, p_all))
+            vv = vv[g.permutation(idx.size)]
+            v[idx] = vv
+            idx = idx[labels[vv] == bu[idx]]
+        keep = u != v
+        return _unique_pairs(u[keep], v[keep], n)
+
+    target = int(round(n * avg_deg / 2))
+    keys = draw(target)
+    for _ in range(3):
+        if keys.size >= target:
+            break
+        keys = _sorted_unique(np.concatenate([keys, draw(target - keys.size)]))
+    return _as_graph(n, keys // n, keys % n, f"dcsbm{n}c{c}", labels)
+
+
 def _rmat_level_tables(probs: np.ndarray, levels: int):
     """Tables mapping a 16-bit uniform to the i- and j-bits of `levels` consecutive R-MAT
     levels (bit t = level t of the group).  The outcome probabilities (products of the
@@ -377,6 +464,11 @@ def workload(name: str) -> dict:
     sbm10k   : SBM N=10,000, 10 clusters, p_in=1e-3, p_out=2e-5, k=10, b=5, m=11, act_max=30
     sbm1m    : SBM N=1,000,000, 100 clusters, d_in=16, d_out=2, k=100, b=20, m=15, act_max=300
     sbm1m_comb: the same graph's combinatorial Laplacian D - S, bounds by 20-step Lanczos
+    dcsbm5m_{lbo|hbo}{lbsv|hbsv}: degree-corrected SBM N=5,000,000, 64 blocks, average degree
+              48.5, 20% (LBO) or 45% (HBO) of edges between blocks, block sizes Dirichlet(200)
+              (LBSV) or Dirichlet(1) (HBSV); k=64, b=16, m=11, act_max=192
+    mawi18m  : connected power-law graph N=18,000,000, average degree 3.0 (Zipf-weighted random
+              recursive tree plus Chung-Lu edges); k=16, b=8, m=15, act_max=96
     knn2m    : kNN-GMM 2,000,000 x 16-D, 50 components, 10-NN, k=50, b=10, m=13, act_max=150
     rmat24   : R-MAT scale 24, ef 16, k=64, b=16, m=15, act_max=192
     Scaled-down variants (for tests) take a suffix, e.g. ``sbm1m@50000`` keeps
@@ -400,6 +492,22 @@ def workload(name: str) -> dict:
                              f"d_out=2, bounds by 20-step Lanczos")
         return dict(graph=gr, k=c, b=20, m=15, act_max=300, tol=tol, v0_seed=0,
                     desc=f"SBM N={n} c={c} d_in=16 d_out=2")
+    if base.startswith("dcsbm5m_") and base[8:] in ("lbolbsv", "lbohbsv", "hbolbsv", "hbohbsv"):
+        n = int(size) if size else 5000000
+        cat = base[8:]
+        between = 0.2 if cat.startswith("lbo") else 0.45
+        var = "low" if cat.endswith("lbsv") else "high"
+        gr = dcsbm_edges(n, 64, 48.5, between, var, seed=10)
+        return dict(graph=gr, k=64, b=16, m=11, act_max=192, tol=tol, v0_seed=0,
+                    desc=f"degree-corrected SBM N={n}, 64 blocks, avg degree 48.5, "
+                         f"{int(between * 100)}% of edges between blocks, {var} block size "
+                         f"variation ({cat.upper()} stand-in)")
+    if base == "mawi18m":
+        n = int(size) if size else 18000000
+        gr = powerlaw_tree_edges(n, 3.0, seed=9)
+        return dict(graph=gr, k=16, b=8, m=15, act_max=96, tol=tol, v0_seed=0,
+                    desc=f"connected power-law graph N={n}, avg degree 3.0, Zipf hubs "
+                         f"(MAWI stand-in)")
     if base == "knn2m":
         n = int(size) if size else 2000000
         gr = knn_gmm_edges(n, seed=3)
