@@ -76,6 +76,8 @@ KM_CASES = [
     (4099, 3, 37, False, 3, None),        # stopped by max_rounds
     (2500, 130, 7, True, 100, 1.0),       # dim > 128
     (1000, 5, 1, True, 100, None),        # one cluster
+    (5000, 200, 200, False, 4, 2.5),      # centroids over 96 KB: blocks staged in turn
+    (3000, 512, 10, True, 100, 1.0),      # the largest dimension
 ]
 
 
