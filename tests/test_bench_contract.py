@@ -1,0 +1,43 @@
+"""bench.py on the CPU: the reference arm's JSON line carries the contract's keys, and the
+partition scores the clustering leg reports agree with the oracle's (pinned against
+scikit-learn and hand-computed values)."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cluster
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_line_keys():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "sbm10k", "--steps", "1", "--warmup", "0"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["higher_is_better"] is False
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+
+
+def test_bench_scores_match_the_oracle():
+    sys.path.insert(0, ROOT)
+    from bench import partition_scores
+    g = synth.rng(3)
+    for _ in range(4):
+        a = g.integers(0, 7, 3000)
+        b = np.where(g.random(3000) < 0.7, a, g.integers(0, 5, 3000))
+        ari, nmi = partition_scores(a, b)
+        assert ari == pytest.approx(cluster.adjusted_rand_index(a, b), abs=1e-12)
+        assert nmi == pytest.approx(cluster.normalized_mutual_info(a, b), abs=1e-12)
+    assert partition_scores([0, 0, 1, 1], [0, 0, 1, 2])[0] == pytest.approx(4 / 7)
