@@ -155,7 +155,7 @@ def replica_throughput(t_job: float, world: int) -> float:
 
 
 def rotation_flops(hist, n):
-    # Step 11 on V only (the CUDA path does not rotate W)
+    # Step 11 on V only: the solver keeps just W's newest k_b columns, which it recomputes
     return sum(2.0 * n * h.k_old * h.k_act for h in hist)
 
 
