@@ -25,9 +25,11 @@ int gemm_tn_chunks(int n) {
   return c < 1 ? 1 : c;
 }
 
+// sym (A = B, ka = kb): outputs enumerate the upper triangle p <= q and each is stored at
+// (p, q) and (q, p) -- the same sums as computing both (fma is symmetric in its factors).
 __global__ void __launch_bounds__(kTnThreads) gemm_tn_partial_kernel(
     int n, const double* __restrict__ A, int lda, int ka, const double* __restrict__ B, int ldb,
-    int kb, double* __restrict__ partial, int out0, int out_count) {
+    int kb, double* __restrict__ partial, int out0, int out_count, int sym) {
   extern __shared__ double sm[];
   double* sA = sm;                       // kTnRows x ka
   double* sB = sm + kTnRows * ka;        // kTnRows x kb
@@ -42,8 +44,24 @@ __global__ void __launch_bounds__(kTnThreads) gemm_tn_partial_kernel(
   for (int i = 0; i < kTnMaxOut; ++i) {
     acc[i] = 0.0;
     int o = out0 + t + i * kTnThreads;
-    pp[i] = (o < out_count + out0 && o < ka * kb) ? o / kb : -1;
-    qq[i] = (pp[i] >= 0) ? o - pp[i] * kb : 0;
+    const int total = sym ? ka * (ka + 1) / 2 : ka * kb;
+    if (o < out_count + out0 && o < total) {
+      if (sym) {
+        int p = 0;
+        while (o >= ka - p) {
+          o -= ka - p;
+          ++p;
+        }
+        pp[i] = p;
+        qq[i] = p + o;
+      } else {
+        pp[i] = o / kb;
+        qq[i] = o - pp[i] * kb;
+      }
+    } else {
+      pp[i] = -1;
+      qq[i] = 0;
+    }
   }
   for (int r0 = r_begin; r0 < r_end; r0 += kTnRows) {
     const int nr = min(kTnRows, r_end - r0);
@@ -69,7 +87,10 @@ __global__ void __launch_bounds__(kTnThreads) gemm_tn_partial_kernel(
   }
 #pragma unroll
   for (int i = 0; i < kTnMaxOut; ++i) {
-    if (pp[i] >= 0) partial[(size_t)chunk * ka * kb + pp[i] * kb + qq[i]] = acc[i];
+    if (pp[i] >= 0) {
+      partial[(size_t)chunk * ka * kb + pp[i] * kb + qq[i]] = acc[i];
+      if (sym) partial[(size_t)chunk * ka * kb + qq[i] * kb + pp[i]] = acc[i];
+    }
   }
 }
 
@@ -83,11 +104,14 @@ cudaError_t launch_gemm_tn_partial(cudaStream_t st, int n, const double* A, int 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const int total = ka * kb;
+  // A^T A: the upper triangle only (half the float64 multiply-adds), mirrored
+  const int sym = (A == B && ka == kb && lda == ldb) ? 1 : 0;
+  const int total = sym ? ka * (ka + 1) / 2 : ka * kb;
   const int per_pass = kTnThreads * kTnMaxOut;
   for (int out0 = 0; out0 < total; out0 += per_pass) {
     gemm_tn_partial_kernel<<<n_chunks, kTnThreads, smem, st>>>(n, A, lda, ka, B, ldb, kb, partial,
-                                                               out0, min(per_pass, total - out0)); note_launch();
+                                                               out0, min(per_pass, total - out0),
+                                                               sym); note_launch();
   }
   return cudaGetLastError();
 }
@@ -182,6 +206,44 @@ cudaError_t launch_gemm_nn_inplace(cudaStream_t st, int n, double* A, int lda, i
                                    const double* B, int ldb, int nb) {
   if (nb > k) return cudaErrorInvalidValue;
   return launch_nn<true>(st, n, A, lda, k, B, ldb, nb, A, lda);
+}
+
+// X(rows, 0:b) <- X(rows, 0:b) U in place, U upper triangular (b x b, ld ldu, b <= 64; the
+// in-block step X R^{-1} of CholQR2).  Column j only needs U(0:j, j): the lanes of a warp are
+// 32 rows sharing one column, so the shortened loop is the same for the whole warp; rows are
+// staged with a padded stride (no shared-memory bank conflicts).  Each output sums k = 0..j in
+// order, as the general kernel does over k = 0..b-1 with zeros beyond j.
+constexpr int kTriRows = 32;
+
+__global__ void __launch_bounds__(kNnThreads) gemm_tri_inplace_kernel(int n, double* __restrict__ X,
+                                                                    int ldx, int b,
+                                                                    const double* __restrict__ U,
+                                                                    int ldu) {
+  extern __shared__ double sx[];   // kTriRows x (b + 1)
+  const int sp = b + 1;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int r0 = blockIdx.x * kTriRows;
+  const int nr = min(kTriRows, n - r0);
+  for (int idx = t; idx < kTriRows * b; idx += kNnThreads) {
+    const int r = idx / b, c = idx - r * b;
+    sx[r * sp + c] = r < nr ? X[(size_t)(r0 + r) * ldx + c] : 0.0;
+  }
+  __syncthreads();
+  for (int col = warp; col < b; col += kNnThreads / 32) {
+    double acc = 0.0;
+    for (int kk = 0; kk <= col; ++kk) acc = fma(sx[lane * sp + kk], __ldg(U + (size_t)kk * ldu + col), acc);
+    if (lane < nr) X[(size_t)(r0 + lane) * ldx + col] = acc;
+  }
+}
+
+cudaError_t launch_gemm_tri_inplace(cudaStream_t st, int n, double* X, int ldx, int b,
+                                    const double* U, int ldu) {
+  if (n <= 0 || b <= 0) return cudaSuccess;
+  if (b > 64) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kTriRows * (b + 1) * sizeof(double);
+  gemm_tri_inplace_kernel<<<ceil_div(n, kTriRows), kNnThreads, smem, st>>>(n, X, ldx, b, U, ldu);
+  note_launch();
+  return cudaGetLastError();
 }
 
 // ---------------- column sums of squares ----------------

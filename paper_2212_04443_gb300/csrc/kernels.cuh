@@ -60,6 +60,9 @@ cudaError_t launch_reduce_partials(cudaStream_t st, const double* partial, int n
 cudaError_t launch_gemm_nn_sub(cudaStream_t st, int n, const double* A, int lda, int k,
                                const double* B, int ldb, int nb, double* C, int ldc);
 // A(:, 0:nb) = A(:, 0:k) B  in place (nb <= k), row tiles staged in shared memory.
+// X(:, 0:b) <- X(:, 0:b) U in place for U upper triangular (b <= 64).
+cudaError_t launch_gemm_tri_inplace(cudaStream_t st, int n, double* X, int ldx, int b,
+                                    const double* U, int ldu);
 cudaError_t launch_gemm_nn_inplace(cudaStream_t st, int n, double* A, int lda, int k,
                                    const double* B, int ldb, int nb);
 // Column sums of squares of X (N x b): per-CTA partials, count b.

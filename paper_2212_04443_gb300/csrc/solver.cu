@@ -412,7 +412,7 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
           ok = false;
           break;
         }
-        HCUDA(launch_gemm_nn_inplace(st, n, X, ldx, b, Rinv, b, b));
+        HCUDA(launch_gemm_tri_inplace(st, n, X, ldx, b, Rinv, b));
       }
       if (ok) return BCHDAV_OK;
       // a failed first pass left X untouched; a failed second pass (never expected after a
