@@ -482,27 +482,43 @@ cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int 
 // Transposed column slices of A's w columns into rows [c0, c0 + w) of planes S x cap x Np,
 // chunk exponents into E[ch * cap + c0 .. + w) for every 1024-row chunk ch < oz_chunks(Np).
 // Rows of the planes outside [c0, c0 + w) are untouched.
+// Transposed slices of columns c_off.. of the planes (S x cap x Np, chunk exponents E): a 64-row
+// x 32-column tile of X staged column-major in shared memory; each lane splits two adjacent
+// rows of one column and stores both digits of a plane as one 4-byte word (a warp writes 128
+// contiguous bytes per plane).  Np is a multiple of 16 and the row even, so the word is aligned
+// and both rows lie in the same 1024-row exponent chunk.
+constexpr int kOzTRows = 64;
+
 __global__ void oz_split_cols_t_off_kernel(int n, const double* __restrict__ X, int ldx, int w, int Np,
                                            int cap, int c_off, const int* __restrict__ E,
                                            __nv_bfloat16* __restrict__ P) {
-  __shared__ double tile[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int r0 = blockIdx.x * 32, cb = blockIdx.y * 32;
-  for (int i = ty; i < 32; i += 8) {
-    const int r = r0 + i, c = cb + tx;
-    tile[i][tx] = (r < n && c < w) ? X[(size_t)r * ldx + c] : 0.0;
+  __shared__ double tile[32][kOzTRows + 1];   // [column][row]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 8 warps
+  const int r0 = blockIdx.x * kOzTRows, cb = blockIdx.y * 32;
+  for (int i = warp; i < kOzTRows; i += 8) {
+    const int r = r0 + i, c = cb + lane;
+    tile[lane][i] = (r < n && c < w) ? X[(size_t)r * ldx + c] : 0.0;
   }
   __syncthreads();
   const size_t plane = (size_t)cap * Np;
-  for (int i = ty; i < 32; i += 8) {
-    const int c = cb + i, r = r0 + tx;
-    if (c >= w || r >= Np) continue;
-    const double a = tile[tx][i];
-    int d[kOzS];
-    oz_digits(oz_fixed(a, E[(size_t)(r / kOzChunk) * cap + c_off + c]), d);
-    const bool neg = a < 0.0;
+  const int r = r0 + 2 * lane;
+  for (int ci = warp; ci < 32; ci += 8) {
+    const int c = cb + ci;
+    if (c >= w) break;
+    if (r >= Np) continue;
+    const double a0 = tile[ci][2 * lane], a1 = tile[ci][2 * lane + 1];
+    const int e = E[(size_t)(r / kOzChunk) * cap + c_off + c];
+    int d0[kOzS], d1[kOzS];
+    oz_digits(oz_fixed(a0, e), d0);
+    oz_digits(oz_fixed(a1, e), d1);
+    const bool n0 = a0 < 0.0, n1 = a1 < 0.0;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(P + (size_t)(c_off + c) * Np + r);
 #pragma unroll
-    for (int s = 0; s < kOzS; ++s) P[s * plane + (size_t)(c_off + c) * Np + r] = oz_bf16(d[s], neg);
+    for (int s = 0; s < kOzS; ++s) {
+      const uint32_t lo = __bfloat16_as_ushort(oz_bf16(d0[s], n0));
+      const uint32_t hi = __bfloat16_as_ushort(oz_bf16(d1[s], n1));
+      dst[s * (plane / 2)] = lo | (hi << 16);
+    }
   }
 }
 
@@ -512,7 +528,7 @@ cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, in
   __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
   oz_col_exp_kernel<<<dim3(oz_chunks(Np), ceil_div(w, 32)), 256, 0, st>>>(n, A, lda, w, cap, c_off,
                                                                            E); note_launch();
-  dim3 g(ceil_div(Np, 32), ceil_div(w, 32));
+  dim3 g(ceil_div(Np, kOzTRows), ceil_div(w, 32));
   oz_split_cols_t_off_kernel<<<g, 256, 0, st>>>(n, A, lda, w, Np, cap, c_off, E, P); note_launch();
   return cudaGetLastError();
 }
