@@ -27,6 +27,9 @@ int gemm_tn_chunks(int n) {
 
 // sym (A = B, ka = kb): outputs enumerate the upper triangle p <= q and each is stored at
 // (p, q) and (q, p) -- the same sums as computing both (fma is symmetric in its factors).
+// MAXOUT outputs per thread per pass: 2 for small Gram matrices (few registers, several CTAs
+// per SM), kTnMaxOut otherwise.
+template <int MAXOUT>
 __global__ void __launch_bounds__(kTnThreads) gemm_tn_partial_kernel(
     int n, const double* __restrict__ A, int lda, int ka, const double* __restrict__ B, int ldb,
     int kb, double* __restrict__ partial, int out0, int out_count, int sym) {
@@ -38,10 +41,10 @@ __global__ void __launch_bounds__(kTnThreads) gemm_tn_partial_kernel(
   const int rows_per = (n + gridDim.x - 1) / gridDim.x;
   const int r_begin = chunk * rows_per;
   const int r_end = min(n, r_begin + rows_per);
-  double acc[kTnMaxOut];
-  int pp[kTnMaxOut], qq[kTnMaxOut];
+  double acc[MAXOUT];
+  int pp[MAXOUT], qq[MAXOUT];
 #pragma unroll
-  for (int i = 0; i < kTnMaxOut; ++i) {
+  for (int i = 0; i < MAXOUT; ++i) {
     acc[i] = 0.0;
     int o = out0 + t + i * kTnThreads;
     const int total = sym ? ka * (ka + 1) / 2 : ka * kb;
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(kTnThreads) gemm_tn_partial_kernel(
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kTnMaxOut; ++i) {
+    for (int i = 0; i < MAXOUT; ++i) {
       if (pp[i] >= 0) {
         double s = acc[i];
 #pragma unroll 4
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(kTnThreads) gemm_tn_partial_kernel(
     }
   }
 #pragma unroll
-  for (int i = 0; i < kTnMaxOut; ++i) {
+  for (int i = 0; i < MAXOUT; ++i) {
     if (pp[i] >= 0) {
       partial[(size_t)chunk * ka * kb + pp[i] * kb + qq[i]] = acc[i];
       if (sym) partial[(size_t)chunk * ka * kb + qq[i] * kb + pp[i]] = acc[i];
@@ -99,19 +102,30 @@ cudaError_t launch_gemm_tn_partial(cudaStream_t st, int n, const double* A, int 
                                    int n_chunks) {
   if (ka <= 0 || kb <= 0) return cudaSuccess;
   size_t smem = (size_t)kTnRows * (ka + kb) * sizeof(double);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tn_partial_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
   // A^T A: the upper triangle only (half the float64 multiply-adds), mirrored
   const int sym = (A == B && ka == kb && lda == ldb) ? 1 : 0;
   const int total = sym ? ka * (ka + 1) / 2 : ka * kb;
+  if (total <= 2 * kTnThreads) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(gemm_tn_partial_kernel<2>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    gemm_tn_partial_kernel<2><<<n_chunks, kTnThreads, smem, st>>>(n, A, lda, ka, B, ldb, kb,
+                                                                  partial, 0, total, sym);
+    note_launch();
+    return cudaGetLastError();
+  }
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tn_partial_kernel<kTnMaxOut>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   const int per_pass = kTnThreads * kTnMaxOut;
   for (int out0 = 0; out0 < total; out0 += per_pass) {
-    gemm_tn_partial_kernel<<<n_chunks, kTnThreads, smem, st>>>(n, A, lda, ka, B, ldb, kb, partial,
-                                                               out0, min(per_pass, total - out0),
-                                                               sym); note_launch();
+    gemm_tn_partial_kernel<kTnMaxOut><<<n_chunks, kTnThreads, smem, st>>>(
+        n, A, lda, ka, B, ldb, kb, partial, out0, min(per_pass, total - out0), sym);
+    note_launch();
   }
   return cudaGetLastError();
 }
