@@ -125,7 +125,16 @@ bchdav_status bchdav_create(bchdav_handle* h, void* cuda_stream);
 bchdav_status bchdav_destroy(bchdav_handle h);
 bchdav_status bchdav_set_stream(bchdav_handle h, void* cuda_stream);
 const char* bchdav_status_string(bchdav_status s);
-const char* bchdav_last_error(bchdav_handle h);   /* NULL handle: last create error */
+/* NULL handle: the message of the last failed call without a handle on this host thread. */
+const char* bchdav_last_error(bchdav_handle h);
+/* Cap the device workspace the handle may hold (bytes; 0, the default, removes the cap).  A
+ * call whose workspace would grow past the cap returns BCHDAV_ERR_OOM, exactly as when
+ * cudaMalloc fails: nothing already held is freed and the handle stays usable (raise the cap,
+ * or call bchdav_release_workspace, and call again).  It bounds what one handle takes on a
+ * device shared with other work.  Not a paper concept. */
+bchdav_status bchdav_set_memory_limit(bchdav_handle h, uint64_t bytes);
+/* Device workspace the handle holds now, in bytes. */
+uint64_t bchdav_workspace_bytes(bchdav_handle h);
 
 /* ---- Eq. (1): the symmetric normalized Laplacian ------------------------ */
 
@@ -190,7 +199,10 @@ bchdav_status bchdav_lanczos_bounds(bchdav_handle h, const bchdav_csr* A, int32_
  * N x k row-major, ld = k (device).  info may be NULL.  Requires 1 <= k <= N,
  * b >= 1, m >= 1, 2b <= act_max and max(dim_max, k + 2b) <= N.
  * Returns BCHDAV_NOT_CONVERGED (with the pairs locked so far, sorted, in the
- * leading info->n_converged slots) when itmax is reached. */
+ * leading info->n_converged slots) when itmax is reached, BCHDAV_ERR_NONFINITE
+ * (before any iteration) when opts->v_init holds a NaN or an infinity, and
+ * BCHDAV_ERR_OOM when the workspace cannot be allocated (or would pass the
+ * handle's bchdav_set_memory_limit cap); the handle stays usable after both. */
 bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int32_t b, int32_t m,
                            int32_t act_max, double tol, const bchdav_opts* opts,
                            double* evals, double* evecs, bchdav_info* info);
@@ -270,8 +282,11 @@ bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, 
 
 /* Step 9: H Y = Y D for the symmetric n x n float64 matrix H (ld_h; only the
  * upper triangle is read).  D: n eigenvalues ascending; Y: n x n, column j the
- * eigenvector of D[j] (row-major, ld_y).  Householder tridiagonalisation and
- * implicit-shift QL, all on the device. */
+ * eigenvector of D[j] (row-major, ld_y).  All on the device: for n <= 32 one
+ * thread block runs Householder tridiagonalisation and implicit-shift QL; for
+ * 32 < n <= 1024 a cooperative grid runs parallel cyclic Jacobi (both give the
+ * same eigenpairs to rounding).  n outside [1, 1024] returns BCHDAV_ERR_ARG.
+ * Synchronises the handle's stream (it reads the convergence status). */
 bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t ld_h, double* D,
                           double* Y, int32_t ld_y);
 
@@ -369,9 +384,12 @@ bchdav_status bchdav_spectral_cluster(bchdav_handle h, int32_t n, int32_t dim, c
  * synchronisation of cudaMalloc/cudaFree).  It uses no handle and calls no
  * cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
  * array inside the library (about 384 KiB per GPU, held until the process
- * exits).  Same arguments and results as bchdav_eigh, plus the CUDA stream
- * (cudaStream_t, NULL = legacy default stream) the work is ordered on; the
- * call synchronises that stream before returning.
+ * exits).  Same arguments as bchdav_eigh, plus the CUDA stream (cudaStream_t,
+ * NULL = legacy default stream) the work is ordered on; the call synchronises
+ * that stream before returning.  It always runs the one-block Householder + QL
+ * kernel (bchdav_eigh's path for n <= 32; for 32 < n <= 128 bchdav_eigh runs
+ * Jacobi instead), so its results equal bchdav_eigh's to rounding, not bit
+ * for bit, and it is slower than bchdav_eigh for the larger n.
  *  - n must be <= 128; larger n returns BCHDAV_ERR_ARG (message via
  *    bchdav_last_error(NULL)).
  *  - The first call on a device looks up the scratch array's device address

@@ -41,7 +41,8 @@ EXPORTED_SYMBOLS = [
     "bchdav_launch_count", "bchdav_gnn_n_params", "bchdav_gnn_forward", "bchdav_gnn_loss_grad",
     "bchdav_gnn_train", "bchdav_gnn_start_block", "bchdav_release_workspace",
     "bchdav_row_normalize", "bchdav_kmeans_seed", "bchdav_kmeans", "bchdav_spectral_cluster",
-    "bchdav_build_laplacian_kind", "bchdav_lanczos_bounds",
+    "bchdav_build_laplacian_kind", "bchdav_lanczos_bounds", "bchdav_set_memory_limit",
+    "bchdav_workspace_bytes",
 ]
 
 
@@ -110,6 +111,8 @@ def lib() -> C.CDLL:
         "bchdav_create": (i32, [C.POINTER(p), p]),
         "bchdav_destroy": (i32, [p]),
         "bchdav_set_stream": (i32, [p, p]),
+        "bchdav_set_memory_limit": (i32, [p, u64]),
+        "bchdav_workspace_bytes": (u64, [p]),
         "bchdav_status_string": (C.c_char_p, [i32]),
         "bchdav_last_error": (C.c_char_p, [p]),
         "bchdav_build_laplacian": (i32, [p, i32, i64, p, p, C.POINTER(CSRStruct)]),
@@ -253,6 +256,13 @@ class Handle:
         if st not in allow:
             raise BchdavError(st, self.L.bchdav_last_error(self.h).decode())
         return st
+
+    def set_memory_limit(self, nbytes: int):
+        """Cap the device workspace this handle may hold (0 removes the cap)."""
+        self._check(self.L.bchdav_set_memory_limit(self.h, int(nbytes)))
+
+    def workspace_bytes(self) -> int:
+        return int(self.L.bchdav_workspace_bytes(self.h))
 
     def set_stream(self, stream):
         self._stream = int(stream)

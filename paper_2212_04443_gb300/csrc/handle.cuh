@@ -43,6 +43,7 @@ struct bchdav_handle_s {
   DevBuf gnn, gnn_opt, gnn_w;   // start-block network: activations, optimiser state, Ritz step
   DevBuf km, km_x;              // clustering: centroids, sums, seeding state; transposed features
   DevBuf lz;                    // Lanczos bound estimate: three vectors, coefficients, T_k
+  DevBuf vchk;                  // count of non-finite entries of a caller's V_init
   const bchdav::SpmmLong* long_rows() const { return lg.n_seg > 0 ? &lg : nullptr; }
   std::vector<bchdav_iter_record> history;
   // filter SpMM schedules found by timing (block size of the row kernel per matrix and width)
@@ -65,11 +66,22 @@ struct bchdav_handle_s {
   double* host_aux = nullptr;
   size_t host_aux_doubles = 0;
 
+  // Cap on the device workspace this handle may hold (bytes; 0 = no cap).  A request that
+  // would exceed it fails with BCHDAV_ERR_OOM before anything is freed, as a failed
+  // cudaMalloc does, so the handle stays usable.
+  size_t mem_limit = 0;
+
   void set_error(bchdav_status, const std::string& m) { err = m; }
 
   bchdav_status ensure(DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return BCHDAV_OK;
+    if (mem_limit > 0 && held_bytes() - b.bytes + bytes > mem_limit) {
+      err = std::string("device allocation of ") + std::to_string(bytes) +
+            " bytes would exceed the handle's workspace limit of " + std::to_string(mem_limit) +
+            " bytes";
+      return BCHDAV_ERR_OOM;
+    }
     b.release();
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
@@ -114,12 +126,25 @@ struct bchdav_handle_s {
     return BCHDAV_OK;
   }
 
-  void release_all() {
+  // every workspace slot (for the accounting of mem_limit and for release_all)
+  template <typename Fn>
+  void for_each_buf(Fn f) {
     DevBuf* all[] = {&V, &W, &Vtmp, &Xo, &F[0], &F[1], &F[2], &F[3], &H, &G, &Y, &D, &part, &eigw,
-                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres, &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part, &tc_err,
-                     &lg_cnt, &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w, &km, &km_x, &lz};
+                     &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres,
+                     &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part, &tc_err, &lg_cnt,
+                     &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w, &km, &km_x,
+                     &lz, &vchk};
+    for (DevBuf* b : all) f(b);
+  }
+  size_t held_bytes() {
+    size_t t = 0;
+    for_each_buf([&](DevBuf* b) { t += b->bytes; });
+    return t;
+  }
+
+  void release_all() {
     lg = bchdav::SpmmLong();
-    for (DevBuf* b : all) b->release();
+    for_each_buf([](DevBuf* b) { b->release(); });
     for (bchdav_handle_s* w : workers) {
       cudaStreamSynchronize(w->stream);
       w->release_all();

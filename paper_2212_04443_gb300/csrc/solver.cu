@@ -17,7 +17,9 @@ using namespace bchdav;
 
 namespace {
 
-std::string g_create_error;
+// Message for entry points without a handle; one per host thread, so that calls made at the
+// same time from different threads (e.g. on different devices) never share the string.
+thread_local std::string g_create_error;
 
 constexpr double kTauDepF64 = 1e-10;
 constexpr double kTauDepMixed = 1e-10;
@@ -522,6 +524,14 @@ bchdav_status bchdav_destroy(bchdav_handle h) {
   return BCHDAV_OK;
 }
 
+bchdav_status bchdav_set_memory_limit(bchdav_handle h, uint64_t bytes) {
+  if (!h) return BCHDAV_ERR_ARG;
+  h->mem_limit = (size_t)bytes;
+  return BCHDAV_OK;
+}
+
+uint64_t bchdav_workspace_bytes(bchdav_handle h) { return h ? (uint64_t)h->held_bytes() : 0; }
+
 bchdav_status bchdav_set_stream(bchdav_handle h, void* stream) {
   if (!h) return BCHDAV_ERR_ARG;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -654,8 +664,9 @@ bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, 
 bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t ld_h, double* D,
                           double* Y, int32_t ld_y) {
   if (!h) return BCHDAV_ERR_ARG;
-  if (n < 1 || n > 4096 || ld_h < n || ld_y < n || !H || !D || !Y) {
-    h->set_error(BCHDAV_ERR_ARG, "eigh: bad arguments");
+  if (n < 1 || n > 1024 || ld_h < n || ld_y < n || !H || !D || !Y) {
+    h->set_error(BCHDAV_ERR_ARG, n > 1024 ? "eigh: n is limited to 1024"
+                                          : "eigh: bad arguments");
     return BCHDAV_ERR_ARG;
   }
   const size_t wd = std::max(eigh_work_doubles(n), eigh_fast_work_doubles(n));
@@ -667,7 +678,7 @@ bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t l
   HCUDA(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HCUDA(cudaStreamSynchronize(h->stream));
   if (st != 0) {
-    h->set_error(BCHDAV_ERR_NONFINITE, "eigh: QL iteration did not converge");
+    h->set_error(BCHDAV_ERR_NONFINITE, "eigh: the iteration did not converge");
     return BCHDAV_ERR_NONFINITE;
   }
   return BCHDAV_OK;
@@ -711,6 +722,23 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   const int k_ri = std::max(act_max / 2, act_max - 3 * b);
   cudaStream_t st = h->stream;
   const double tau_dep = prec == BCHDAV_PREC_MIXED ? kTauDepMixed : kTauDepF64;
+
+  // A caller's initial block must be finite: one NaN would spread through the filter into
+  // every later vector.  Checked once here (one pass over N x k_init) so that such an input
+  // fails at once with BCHDAV_ERR_NONFINITE instead of after a wasted iteration.
+  if (opts.k_init > 0) {
+    BCHDAV_TRY(h->ensure(h->vchk, sizeof(int)));
+    BCHDAV_TRY(h->ensure_pinned(1024));
+    HCUDA(cudaMemsetAsync(h->vchk.p, 0, sizeof(int), st));
+    HCUDA(launch_check_finite(st, N, opts.k_init, opts.v_init, opts.ld_v_init, h->vchk.as<int>()));
+    int* flag_h = reinterpret_cast<int*>(h->host_pinned);
+    HCUDA(cudaMemcpyAsync(flag_h, h->vchk.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HCUDA(cudaStreamSynchronize(st));
+    if (*flag_h != 0) {
+      h->set_error(BCHDAV_ERR_NONFINITE, "solve: v_init holds a non-finite value");
+      return BCHDAV_ERR_NONFINITE;
+    }
+  }
 
   // ---- workspace
   // W = A V (Algorithm 2, Steps 7, 11, 14): only its newest k_b columns are ever read (Step 8
