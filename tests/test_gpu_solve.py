@@ -151,16 +151,21 @@ def test_sbm10k_workload(H):
     # eigenvalue returned (~1e-4 here), so allow tol / that value with a safety factor
     gap = ev[~zero].min() if (~zero).any() else 1.0
     assert np.linalg.norm(Z - U @ (U.T @ Z), axis=0).max() < 4 * TOL / gap
-    # parity with the oracle while the trajectories agree (they agree until a degenerate
-    # cluster of Ritz values makes the choice of basis arbitrary)
+    # parity with the oracle: the eigenvalues, compared unconditionally.  The lock counts
+    # agree until the null-space cluster of Ritz values (1,064 exact zeros) decides which
+    # vectors are tested: rounding orders equal Ritz values, so from there the trajectories
+    # may part (on GB300 they agree for the first 53 of ~118 iterations) while both runs
+    # still return the same eigenvalues.
     n_same = 0
     for a, o in zip(hist, r.history):
         if a.k_c != o["k_c"]:
             break
         n_same += 1
-    assert n_same >= 5
-    if n_same == len(r.history) == len(hist):
-        assert np.abs(ev - r.evals).max() <= 1e-10
+    err = np.abs(ev - r.evals).max()
+    print(f"sbm10k: k_c agree for {n_same} of {len(r.history)} oracle iterations "
+          f"({len(hist)} on the GPU); max |lambda - lambda_oracle| = {err:.3e}")
+    assert n_same >= 50
+    assert err <= 1e-10
 
 
 def test_mixed_precision_reaches_tol(H):

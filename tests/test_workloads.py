@@ -49,3 +49,65 @@ def test_dcsbm_categories(cat):
     else:
         assert sizes.max() / sizes.min() > 10
     assert w["k"] == 64 and np.unique(g.labels).size == 64
+
+
+def test_knn_gmm_exact_neighbours():
+    """The kNN-GMM workload (Gaussian mixture in 16-D, 10 nearest neighbours): every node's
+    out-edges are exactly its 10 nearest other points by float64 Euclidean distance (ties to the
+    lower index), checked by brute force; the graph the Laplacian is built from is their
+    symmetrisation (an undirected edge wherever either end lists the other)."""
+    n, dim, knn = 3000, 16, 10
+    g = synth.knn_gmm_edges(n, dim=dim, n_comp=50, knn=knn, seed=3)
+    # the generator's points, redrawn from the same seeded stream
+    r = synth.rng(3)
+    means = r.uniform(-10.0, 10.0, (50, dim))
+    comp = r.integers(0, 50, n)
+    x = means[comp] + r.standard_normal((n, dim))
+    assert np.array_equal(g.labels, comp)
+    d2 = ((x[:, None, :] - x[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    want = np.argsort(d2, axis=1, kind="stable")[:, :knn]
+    assert np.all(g.src != g.dst)
+    assert np.all(np.bincount(g.src, minlength=n) == knn)
+    order = np.lexsort((g.dst, g.src))
+    got = g.dst[order].reshape(n, knn)
+    assert np.array_equal(np.sort(got, axis=1), np.sort(want, axis=1))
+    # symmetrised degree: at least knn per node, at most knn + in-degree
+    A = sp.coo_matrix((np.ones(g.src.size), (g.src, g.dst)), shape=(n, n)).tocsr()
+    S = ((A + A.T) > 0).astype(np.int8)
+    deg = np.asarray(S.sum(axis=1)).ravel()
+    assert deg.min() >= knn and deg.max() <= knn + np.bincount(g.dst, minlength=n).max()
+    assert S.diagonal().sum() == 0
+    g2 = synth.knn_gmm_edges(n, dim=dim, n_comp=50, knn=knn, seed=3)
+    assert np.array_equal(g2.src, g.src) and np.array_equal(g2.dst, g.dst)
+
+
+def test_knn_gmm_reduced_workload_components():
+    """The 200,000-point reduction of the kNN-GMM workload has one connected component per
+    mixture component (50), so lambda = 0 has multiplicity 50 = k.  The oracle goldens record
+    what Algorithm 2 finds there: from k Gaussian start columns it returns all 50 null
+    directions; from k_b = 10 it returns fewer, because the filter is the identity on the null
+    space (p(0) = 1) and only rounding noise brings null directions beyond the span of the
+    start block into the basis (locking then skips copies of the multiple eigenvalue)."""
+    import json
+    import os
+    w = synth.workload("knn2m@200000")
+    g = w["graph"]
+    n = g.n
+    A = sp.coo_matrix((np.ones(g.src.size), (g.src, g.dst)), shape=(n, n))
+    ncomp, lab = csgraph.connected_components(A, directed=False)
+    assert ncomp == 50
+    # components never mix mixture components
+    assert np.all(np.bincount(lab, minlength=ncomp) > 0)
+    assert all(np.unique(g.labels[lab == c]).size == 1 for c in range(ncomp))
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+    def zeros(name):
+        with open(os.path.join(here, name)) as f:
+            gold = json.load(f)
+        return int(np.sum(np.abs(np.asarray(gold["evals"])) < 1e-10)), gold
+
+    z_k, gk = zeros("oracle_knn2m@200000_v0k.json")
+    z_b, gb = zeros("oracle_knn2m@200000.json")
+    assert gk["v0_cols"] == 50 and z_k == ncomp
+    assert z_b < ncomp
