@@ -49,35 +49,31 @@ __device__ __forceinline__ void stv(T* __restrict__ p, const T (&v)[VW]) {
   *reinterpret_cast<V*>(p) = x;
 }
 
+// The row's nonzeros in batches of four: the four colidx/val loads are independent, then the
+// four gathers.  A batch past the row's end loads the row's own X row (in bounds, read again
+// by the epilogue) and skips its multiply-add, so a row of length L costs ceil(L / 4)
+// dependent load rounds and the sum runs in the order of the nonzeros (k ascending).
 template <typename T, int VW>
 __device__ __forceinline__ void row_product(const int* __restrict__ colidx, const T* __restrict__ val,
-                                            const T* __restrict__ X, int ldx, int c0, int start,
-                                            int end, T (&acc)[VW]) {
-  int k = start;
-  for (; k + 3 < end; k += 4) {
-    int j0 = __ldg(colidx + k), j1 = __ldg(colidx + k + 1);
-    int j2 = __ldg(colidx + k + 2), j3 = __ldg(colidx + k + 3);
-    T a0 = __ldg(val + k), a1 = __ldg(val + k + 1), a2 = __ldg(val + k + 2), a3 = __ldg(val + k + 3);
-    T x0[VW], x1[VW], x2[VW], x3[VW];
-    ldv<T, VW>(X + (size_t)j0 * ldx + c0, x0);
-    ldv<T, VW>(X + (size_t)j1 * ldx + c0, x1);
-    ldv<T, VW>(X + (size_t)j2 * ldx + c0, x2);
-    ldv<T, VW>(X + (size_t)j3 * ldx + c0, x3);
+                                            const T* __restrict__ X, int ldx, int c0, int row,
+                                            int start, int end, T (&acc)[VW]) {
+  for (int k = start; k < end; k += 4) {
+    int j[4];
+    T a[4];
 #pragma unroll
-    for (int i = 0; i < VW; ++i) {
-      acc[i] = fma(a0, x0[i], acc[i]);
-      acc[i] = fma(a1, x1[i], acc[i]);
-      acc[i] = fma(a2, x2[i], acc[i]);
-      acc[i] = fma(a3, x3[i], acc[i]);
+    for (int u = 0; u < 4; ++u) {
+      const bool ok = k + u < end;
+      j[u] = ok ? __ldg(colidx + k + u) : row;
+      a[u] = ok ? __ldg(val + k + u) : T(0);
     }
-  }
-  for (; k < end; ++k) {
-    int j = __ldg(colidx + k);
-    T a = __ldg(val + k);
-    T x[VW];
-    ldv<T, VW>(X + (size_t)j * ldx + c0, x);
+    T x[4][VW];
 #pragma unroll
-    for (int i = 0; i < VW; ++i) acc[i] = fma(a, x[i], acc[i]);
+    for (int u = 0; u < 4; ++u) ldv<T, VW>(X + (size_t)j[u] * ldx + c0, x[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k + u < end)
+#pragma unroll
+        for (int i = 0; i < VW; ++i) acc[i] = fma(a[u], x[u][i], acc[i]);
   }
 }
 
@@ -215,7 +211,7 @@ __global__ void __launch_bounds__(512) spmm_axpby_kernel(
 #pragma unroll
       for (int i = 0; i < VW; ++i) acc[i] += pseg[s * b + c0 + i];
   } else {
-    row_product<T, VW>(colidx, val, X, ldx, c0, p0, p1, acc);
+    row_product<T, VW>(colidx, val, X, ldx, c0, row, p0, p1, acc);
   }
   T out[VW];
 #pragma unroll
