@@ -53,8 +53,8 @@ def parse():
     ap.add_argument("--no-cluster", action="store_true",
                     help="skip Steps 4-5 (row normalisation + k-means) after the solve")
     ap.add_argument("--dense-path", type=int, default=0, choices=[0, 1, 2],
-                    help="0: slice products on warp-level mma; 1: float64 FMA kernels; "
-                         "2: row-operand slice products on tcgen05")
+                    help="0: slice products on tcgen05 (default); 1: float64 FMA kernels; "
+                         "2: slice products on the legacy warp-level mma")
     return ap.parse_args()
 
 
@@ -166,9 +166,19 @@ def slice_pairs(S):
     return S * (S + 1) // 2
 
 
-# DRAM bytes per Step-11 rotation launch (mixed path, 1M-node SBM): ncu capture at N = 200,000
-# scaled by N (profiles/oz_gemm_rotation_traffic.md); valid for the kernel as captured
-ROTATION_TRAFFIC_BYTES = {"mixed": 3.33e9}
+# DRAM bytes (read + write) per launch of the filter SpMM (spmm_axpby_kernel<float, 4>, one
+# residual-form step) on the 1M-node SBM, from the ncu capture of the current kernel
+# (profiles/spmm_axpby_f32_sbm1m.md); None when no capture of the current kernel exists
+FILTER_TRAFFIC_BYTES = {"sbm1m": None}
+
+
+def filter_model_bytes(n, nnz, b, m, iters, s):
+    """Compulsory bytes of the filter SpMM per solve by the scope table's model: per step
+    4 (N + 1) + nnz (4 + s) + 3 N b s (the first step of a filter 2 N b s), m steps per filter,
+    one filter per outer iteration; s = value and vector element bytes."""
+    csr = 4.0 * (n + 1) + nnz * (4.0 + s)
+    per_filter = m * csr + (2 + 3 * (m - 1)) * n * b * s
+    return iters * per_filter
 
 # pairs per float64-equivalent flop of each component, by path
 PAIRS = {
@@ -251,8 +261,10 @@ def run_ours(args):
 
     # ---- per-component roofline of the timed solve
     n = g.n
+    sx = 4.0 if prec == P.PREC_MIXED else 8.0
+    model_bytes = filter_model_bytes(n, A.nnz, b, m, info.iters, sx)
     comp = {
-        "filter": dict(ms=info.ms["filter"], work=info.filter_bytes, bound="hbm", unit="GB/s"),
+        "filter": dict(ms=info.ms["filter"], work=model_bytes, bound="hbm", unit="GB/s"),
         "rotation": dict(ms=info.ms["rot"], work=rotation_flops(hist, n), unit="TFLOP/s"),
         "orthonormalisation": dict(ms=info.ms["orth"], work=orth_flops(hist, n, b), unit="TFLOP/s"),
         "rayleigh_quotient": dict(ms=info.ms["h"], work=h_flops(hist, n, b), unit="TFLOP/s"),
@@ -265,41 +277,44 @@ def run_ours(args):
             c["achieved"] = c["work"] / s / 1e9 if s > 0 else 0.0
             c["peak"] = hbm_peak
         elif tensor_path:
-            # products executed as slice-pair bf16 tensor-core products
+            # products executed as slice-pair bf16 tensor-core products: the method's own
+            # float64 flop rate beside the rate of bf16 slice work it costs
             pairs = PAIRS["mixed" if prec == P.PREC_MIXED else "f64"][name]
             c["bound"] = "tensor"
             c["slice_pairs"] = pairs
-            c["fp64_equiv_tflops"] = c["work"] / s / 1e12 if s > 0 else 0.0
+            c["method_fp64_tflops"] = c["work"] / s / 1e12 if s > 0 else 0.0
             c["achieved"] = pairs * c["work"] / s / 1e12 if s > 0 else 0.0
             c["peak"] = bf16_peak
         else:
             c["bound"] = "alu"
             c["achieved"] = c["work"] / s / 1e12 if s > 0 else 0.0
             c["peak"] = FP64_PEAK_TFLOPS
-    # the rotation (Step 11) is one kernel family with a clean FLOP count; it and the
-    # filter SpMM are the two kernels whose rates are reported
-    dc = comp["rotation"]
-    roofline = {"kernel": "oz_gemm_kernel (Step 11 rotation, digit slices on bf16 tensor cores)"
-                if tensor_path else "gemm_nn_kernel (Step 11, float64)",
-                "bound": dc["bound"], "achieved": round(dc["achieved"], 3),
-                "peak": dc["peak"], "unit": dc["unit"],
-                "frac": round(dc["achieved"] / dc["peak"], 4),
-                "traffic": (ROTATION_TRAFFIC_BYTES.get("mixed") if tensor_path and dense_path == 0
-                            and prec == P.PREC_MIXED and args.workload == "sbm1m" else None),
-                "traffic_note": "DRAM bytes per Step-11 launch: ncu capture at N=200,000 scaled "
-                                "by N (profiles/oz_gemm_rotation_traffic.md)",
-                "fp64_equivalent_tflops": round(dc.get("fp64_equiv_tflops", dc["achieved"]), 3),
-                "slice_pairs": dc.get("slice_pairs"),
-                "note": "achieved counts the bf16 tensor FLOPs of the slice products (slice_pairs "
-                        "per float64-equivalent flop) over the Step-11 time including operand "
-                        "slicing",
-                "peak_source": (f"{bf16_kind} bf16 (MEASURED_PEAKS.json)" if tensor_path else
-                                "nominal FP64 rate (2 DFMA/clk/SM); probe measured 1.19-1.20")}
+    # The metric names the filter SpMM: its rate by the scope table's compulsory-byte model
+    # (CSR once, each row of X once, the previous block once, the output once) is the line's
+    # roofline; the residual-form operands the kernel also streams are reported beside it.
     fc = comp["filter"]
-    filter_roof = {"bound": "hbm", "achieved": round(fc["achieved"], 1), "peak": hbm_peak,
-                   "unit": "GB/s", "frac": round(fc["achieved"] / hbm_peak, 4),
-                   "bytes_per_solve": fc["work"], "ms_per_solve": round(fc["ms"], 3),
-                   "peak_source": peak_kind}
+    ms_f = fc["ms"]
+    kern_bytes = info.filter_bytes
+    launches = info.iters * m
+    roofline = {
+        "kernel": "spmm_axpby_kernel<float, 4> (filter SpMM, Algorithm 3)" if prec == P.PREC_MIXED
+        else "spmm_axpby_kernel<double, 2> (filter SpMM, Algorithm 3)",
+        "bound": "hbm", "achieved": round(fc["achieved"], 1), "peak": hbm_peak, "unit": "GB/s",
+        "frac": round(fc["achieved"] / hbm_peak, 4),
+        "traffic": (FILTER_TRAFFIC_BYTES.get(args.workload) if prec == P.PREC_MIXED else None),
+        "model_bytes_per_launch": round(model_bytes / launches),
+        "launch_us": round(ms_f * 1e3 / launches, 2),
+        "note": "achieved = scope-table model bytes of the filter's m SpMM steps per outer "
+                "iteration / the filter's device time (CUDA events around each filter)",
+        "peak_source": f"{peak_kind} HBM copy rate (MEASURED_PEAKS.json)"}
+    filter_roof = {"bound": "hbm", "model_gbs": round(fc["achieved"], 1),
+                   "model_frac": round(fc["achieved"] / hbm_peak, 4),
+                   "model_bytes_per_solve": model_bytes,
+                   "kernel_bytes_per_solve": kern_bytes,
+                   "kernel_gbs": round(kern_bytes / (ms_f / 1e3) / 1e9, 1) if ms_f > 0 else 0.0,
+                   "kernel_bytes_note": "what the kernel streams: also the residual operand R and "
+                                        "the own-row read of X (residual-form filter)",
+                   "ms_per_solve": round(ms_f, 3), "peak": hbm_peak, "peak_source": peak_kind}
     breakdown = {kk: round(v, 3) for kk, v in info.ms.items()}
     components = {kk: {key: (round(v, 3) if isinstance(v, float) else v)
                        for key, v in c.items() if key != "work"} for kk, c in comp.items()}

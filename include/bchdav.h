@@ -77,10 +77,10 @@ typedef struct {
   int32_t dim_max;          /* 0: min(max(act_max + 2b, k + 30), N)  (Sec. 4 defaults) */
   int32_t itmax;            /* 0: 1000 outer iterations */
   int32_t precision;        /* bchdav_precision */
-  int32_t dense_path;       /* 0: float64-accurate tensor-core products (split into bf16 slices,
-                               warp-level mma) for Steps 6, 8 and 11; 1: plain float64 FMA
-                               kernels; 2: as 0 with the row-operand products (Step 6 update,
-                               Step 11 rotation) on tcgen05 (tensor memory accumulators) */
+  int32_t dense_path;       /* Steps 6, 8 and 11: 0 (default): float64-accurate products from
+                               bf16 digit slices on tcgen05 (tensor-memory level sums); 1: plain
+                               float64 FMA kernels; 2: the same slice products on the legacy
+                               warp-level mma.sync (kept for comparison) */
   uint64_t seed;            /* seed of the random vectors the method draws (Philox4x32-10) */
   const double* v_init;     /* optional N x k_init initial block (Algorithm 2, V_init) */
   int32_t k_init;
@@ -268,15 +268,19 @@ bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V,
                                     double tau_dep, int64_t* rep_counter, int32_t* n_replaced);
 
 /* Steps 6 and 8: out (ka x kb, row-major, ld = kb) = A^T B for the N x ka block A (lda)
- * and the N x kb block B (ldb), by the float64-accurate tensor-core product (dense_path 0)
- * or plain float64 FMAs (dense_path 1).  Deterministic (fixed reduction order). */
+ * and the N x kb block B (ldb), by the float64-accurate slice product on tcgen05 (dense_path
+ * 0), plain float64 FMAs (dense_path 1) or the slice product on warp-level mma (dense_path 2).
+ * Deterministic (fixed reduction order).  BCHDAV_ERR_TIMEOUT if a bounded device wait of the
+ * tcgen05 kernel expired (nothing faults; the handle stays usable).  Synchronises the stream
+ * on dense_path 0. */
 bchdav_status bchdav_gram(bchdav_handle h, int32_t n, const double* A, int32_t lda, int32_t ka,
                           const double* B, int32_t ldb, int32_t kb, double* out,
                           int32_t dense_path);
 
 /* Step 11: V(:, 0:nb) = V(:, 0:k) Y in place (V: n x k, ldv; Y: k x nb, ld_y; nb <= k),
- * the subspace rotation, with the same float64-accurate tensor-core product the
- * solver uses (dense_path 0) or plain float64 FMAs (dense_path 1). */
+ * the subspace rotation, with the products of bchdav_gram's dense_path (0: tcgen05, 1: float64
+ * FMAs, 2: warp-level mma; the tensor-core paths need k <= 448).  BCHDAV_ERR_TIMEOUT as for
+ * bchdav_gram. */
 bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, int32_t k,
                             const double* Y, int32_t ld_y, int32_t nb, int32_t dense_path);
 

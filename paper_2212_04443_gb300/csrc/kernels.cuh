@@ -108,8 +108,11 @@ size_t ozaki_nn_work_bytes(int n, int K, int nb);
 bool ozaki_nn_supported(int K);
 // out (ka x kb, row-major) = A^T B for A N x ka, B N x kb (any N: the reduction is cut
 // into pieces of 1024 rows whose float32 sums are exact, folded in float64).
+// tc_err non-NULL: the products run on tcgen05 (launch_tc_gram), which sets *tc_err when one
+// of its bounded waits expired.
 cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, int ka,
-                            const double* B, int ldb, int kb, double* out, void* work);
+                            const double* B, int ldb, int kb, double* out, void* work,
+                            int* tc_err = nullptr);
 size_t ozaki_tn_work_bytes(int n, int ka, int kb);
 // Building blocks with caller-kept slices ("planes": 8 bf16 digit planes plus exponents).
 int oz_chunks(int Np);   // 1024-row exponent chunks of a Gram operand with Np rows
@@ -133,6 +136,11 @@ cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void*
 cudaError_t oz_nn_from_planes_tc(cudaStream_t st, int n, int K, int Kp, const void* PA,
                                  const int* EA, const double* B, int ldb, int nb, double* C,
                                  int ldc, bool subtract, void* bwork, int slices, int* err);
+// Gram product A^T B of transposed column planes on tcgen05 (tc05.cu); same operands as
+// oz_gram_from_planes, plus err (device int, set when a bounded wait expired).
+cudaError_t launch_tc_gram(cudaStream_t st, int Np, const void* PA, const int* EA, int capA, int a0,
+                           int ka, const void* PB, const int* EB, int capB, int kb, double* out,
+                           double* partial, int slices, int* err);
 cudaError_t launch_tc_slice_nn(cudaStream_t st, int n, int nb, int Kp, const void* PA,
                                const int* EA, const void* PB, int nbp, const int* EB, double* C,
                                int ldc, bool subtract, int slices, int* err);

@@ -47,6 +47,17 @@ constexpr int kOzStages = 3;     // cp.async pipeline depth
 __device__ __forceinline__ int oz_sw(int r, int half) { return r * 16 + ((half ^ ((r >> 2) & 1)) << 3); }
 constexpr int kOzChunk = 1024;   // rows per exponent chunk of a Gram operand (64 k steps of 16)
 
+// Digit planes are stored tiled for the tensor cores.  Element (s, r, k) of the planes of an
+// operand with `rows` rows (k the reduction index, padded to a multiple of 16) sits at
+//     ((((k / 16) * 8 + s) * 2 + (k / 8) % 2) * rows + r) * 8 + k % 8      (bf16 units),
+// so that one 16-wide k step of any run of consecutive rows is, for each slice and each half of
+// the step, one contiguous block of 16 bytes per row: the K-major 8 x 16-byte core matrices the
+// tcgen05 products read (a 128-row tile: 2 KB per slice and half, fetched by one TMA box for all
+// slices), and 16-byte pieces at consecutive addresses for the warp-level kernel's cp.async.
+__host__ __device__ __forceinline__ size_t oz_tix(int s, size_t r, int k, size_t rows) {
+  return (((((size_t)(k >> 4) * kOzS + s) * 2 + ((k >> 3) & 1)) * rows + r) << 3) + (k & 7);
+}
+
 // --- digit extraction ------------------------------------------------------
 __device__ __forceinline__ int oz_exp_plus1(double a) {
   // e + 1 where |a| = 1.m * 2^e; very small (subnormal) values count as zero
@@ -102,21 +113,50 @@ __global__ void oz_row_exp_kernel(int n, const double* __restrict__ A, int lda, 
   }
 }
 
-// Slices of A: planes S x N x Kp (row-major, zero padded in k).
-__global__ void oz_split_rows_kernel(int n, const double* __restrict__ A, int lda, int K, int Kp,
-                                     const int* __restrict__ E, __nv_bfloat16* __restrict__ P) {
-  const size_t plane = (size_t)n * Kp;
-  const long long total = (long long)n * Kp;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / Kp), k = (int)(idx - (long long)r * Kp);
-    const double a = (k < K) ? A[(size_t)r * lda + k] : 0.0;
-    int d[kOzS];
-    oz_digits(oz_fixed(a, E[r]), d);
-    const bool neg = a < 0.0;
-#pragma unroll
-    for (int s = 0; s < kOzS; ++s) P[s * plane + idx] = oz_bf16(d[s], neg);
+// Slices of A (N x K) into tiled planes with `n` rows and Kp (zero padded) values of k.  A
+// tile of 64 rows x 32 k is staged in shared memory with row-contiguous (coalesced) loads;
+// thread t then splits 8 consecutive k of row t % 64 and stores one 16-byte piece per slice
+// (consecutive threads: consecutive rows, 1 KB contiguous per slice and half k step).
+constexpr int kOzSRows = 64, kOzSK = 32;
+
+__global__ void __launch_bounds__(256) oz_split_rows_kernel(int n, const double* __restrict__ A,
+                                                            int lda, int K, int Kp,
+                                                            const int* __restrict__ E,
+                                                            __nv_bfloat16* __restrict__ P) {
+  __shared__ double tile[kOzSRows][kOzSK + 1];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int r0 = blockIdx.x * kOzSRows, k0 = blockIdx.y * kOzSK;
+  for (int i = warp; i < kOzSRows; i += 8) {
+    const int r = r0 + i, k = k0 + lane;
+    tile[i][lane] = (r < n && k < K) ? A[(size_t)r * lda + k] : 0.0;
   }
+  __syncthreads();
+  const int rl = t & (kOzSRows - 1), g = t >> 6;   // 4 groups of 8 k
+  const int r = r0 + rl, kg = k0 + 8 * g;
+  if (r >= n || kg >= Kp) return;
+  const int e = E[r];
+  uint32_t w[kOzS][4];
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    const double a0 = tile[rl][8 * g + j], a1 = tile[rl][8 * g + j + 1];
+    int d0[kOzS], d1[kOzS];
+    oz_digits(oz_fixed(a0, e), d0);
+    oz_digits(oz_fixed(a1, e), d1);
+#pragma unroll
+    for (int s = 0; s < kOzS; ++s)
+      w[s][j >> 1] = (uint32_t)__bfloat16_as_ushort(oz_bf16(d0[s], a0 < 0.0)) |
+                     ((uint32_t)__bfloat16_as_ushort(oz_bf16(d1[s], a1 < 0.0)) << 16);
+  }
+#pragma unroll
+  for (int s = 0; s < kOzS; ++s)
+    *reinterpret_cast<uint4*>(P + oz_tix(s, r, kg, n)) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+}
+
+static void oz_split_rows_launch(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
+                                 const int* E, __nv_bfloat16* P) {
+  dim3 g(ceil_div(n, kOzSRows), ceil_div(Kp, kOzSK));
+  oz_split_rows_kernel<<<g, 256, 0, st>>>(n, A, lda, K, Kp, E, P);
+  note_launch();
 }
 
 // Column exponents and transposed slices of B (K x nb): planes S x nbp x Kp.
@@ -124,7 +164,6 @@ __global__ void oz_split_cols_kernel(int K, int nb, const double* __restrict__ B
                                      int nbp, int* __restrict__ F_out, __nv_bfloat16* __restrict__ P) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  const size_t plane = (size_t)nbp * Kp;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nbp; c += warps) {
     int m = -100000;
     if (c < nb)
@@ -138,7 +177,7 @@ __global__ void oz_split_cols_kernel(int K, int nb, const double* __restrict__ B
       oz_digits(oz_fixed(b, Ec), d);
       const bool neg = b < 0.0;
 #pragma unroll
-      for (int s = 0; s < kOzS; ++s) P[s * plane + (size_t)c * Kp + k] = oz_bf16(d[s], neg);
+      for (int s = 0; s < kOzS; ++s) P[oz_tix(s, c, k, nbp)] = oz_bf16(d[s], neg);
     }
   }
 }
@@ -169,8 +208,8 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Slice product.  Rows of the result come from the planes PA (S x M x Kp, k contiguous),
-// columns from PB (S x Np x Kp).  CTA: 8 warps as 4 (rows) x 2 (cols), warp tile 16 x 16 (one
+// Slice product.  Rows of the result come from rows a0 .. a0 + M - 1 of the tiled planes PA
+// (Ma rows), columns from the tiled planes PB (Np rows).  CTA: 8 warps as 4 (rows) x 2 (cols), warp tile 16 x 16 (one
 // m16 tile, two n8 tiles); k steps of 16 double-buffered through shared memory.  blockIdx.z
 // takes k steps [z * k_split, (z + 1) * k_split).  The float32 level sums are folded into
 // float64 every kOzFlush k steps (1024 values of k, inside the exactness bound) and at the end.
@@ -180,7 +219,8 @@ constexpr int kOzFlush = 64;
 // NS: leading digit slices used (8: float64-accurate; fewer: a truncated product whose
 // operands keep 6 NS bits, for the first DGKS pass that the second one corrects)
 template <int MODE, int NS>
-__global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, int Kp, int k_split,
+__global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int a0, int N, int Kp,
+                                                      int k_split,
                                                       const __nv_bfloat16* __restrict__ PA,
                                                       const int* __restrict__ EA,
                                                       const __nv_bfloat16* __restrict__ PB, int Np,
@@ -200,7 +240,6 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
   const int nct = Np / kOzBN;
   const int r0 = MODE == 2 ? blockIdx.x * kOzBM : (int)(blockIdx.x / nct) * kOzBM;
   const int c0 = MODE == 2 ? blockIdx.y * kOzBN : (int)(blockIdx.x % nct) * kOzBN;
-  const size_t planeA = (size_t)Ma * Kp, planeB = (size_t)Np * Kp;
   const int g = lane >> 2, tig = lane & 3;
   const int nk_all = Kp / kOzBK;
   const int kt0 = blockIdx.z * k_split;
@@ -211,14 +250,14 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
       const int s = q / (kOzBM * 2), rem = q - s * kOzBM * 2, row = rem >> 1, half = rem & 1;
       const int gr = r0 + row;
       __nv_bfloat16* dst = &sA[buf][s][oz_sw(row, half)];
-      if (gr < M) cp_async16(dst, PA + s * planeA + (size_t)gr * Kp + k0 + half * 8);
+      if (gr < M) cp_async16(dst, PA + oz_tix(s, (size_t)a0 + gr, k0 + half * 8, Ma));
       else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
     for (int q = t; q < NS * kOzBN * 2; q += 256) {
       const int s = q / (kOzBN * 2), rem = q - s * kOzBN * 2, row = rem >> 1, half = rem & 1;
       const int gc = c0 + row;
       __nv_bfloat16* dst = &sB[buf][s][oz_sw(row, half)];
-      if (gc < Np) cp_async16(dst, PB + s * planeB + (size_t)gc * Kp + k0 + half * 8);
+      if (gc < Np) cp_async16(dst, PB + oz_tix(s, gc, k0 + half * 8, Np));
       else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
     cp_async_commit();
@@ -239,15 +278,25 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
         for (int e = 0; e < 4; ++e) acc[L][j][e] = 0.f;
   };
   // MODE 2: chunk exponents, the k steps folded last lie in chunk `ch`
+  // The level sums are integers (exact in float32), so they are combined exactly in 64-bit
+  // integers and converted to float64 once: hi = sum_{L < H} acc_L 2^(6 (H - 1 - L)) and
+  // lo = sum_{L >= H} acc_L 2^(6 (NS - 1 - L)), H = NS / 2, each below 2^42 for the 1024-row
+  // pieces of a Gram product; value = (hi 2^(6 (NS - H)) + lo) 2^(-6 (NS + 1)).
   auto flush = [&](int ch) {
+    constexpr int kH = NS / 2;
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        double v = 0.0;
+        long long hi = 0, lo = 0;
 #pragma unroll
-        for (int L = NS - 1; L >= 0; --L)
-          v = fma((double)acc[L][j][e], __longlong_as_double((long long)(1023 - kOzBits * (L + 2)) << 52), v);
+        for (int L = 0; L < NS; ++L) {
+          const long long q = (long long)__float2int_rn(acc[L][j][e]);
+          if (L < kH) hi += q * (1LL << (kOzBits * (kH - 1 - L)));
+          else lo += q * (1LL << (kOzBits * (NS - 1 - L)));
+        }
+        double v = fma((double)hi, (double)(1LL << (kOzBits * (NS - kH))), (double)lo) *
+                   __longlong_as_double((long long)(1023 - kOzBits * (NS + 1)) << 52);
         if (MODE == 2) {
           const int row = r0 + wm * 16 + g + (e >> 1) * 8;
           const int col = c0 + wn * 16 + j * 8 + tig * 2 + (e & 1);
@@ -323,17 +372,18 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(int M, int Ma, int N, i
 }
 
 template <int MODE, int NS = kOzS>
-static cudaError_t oz_launch_gemm(cudaStream_t st, dim3 grid, int M, int Ma, int N, int Kp, int k_split,
-                                  const __nv_bfloat16* PA, const int* EA, const __nv_bfloat16* PB,
-                                  int Np, const int* EB, double* C, int ldc) {
+static cudaError_t oz_launch_gemm(cudaStream_t st, dim3 grid, int M, int Ma, int a0, int N, int Kp,
+                                  int k_split, const __nv_bfloat16* PA, const int* EA,
+                                  const __nv_bfloat16* PB, int Np, const int* EB, double* C,
+                                  int ldc) {
   const size_t smem = sizeof(__nv_bfloat16) * kOzStages * kOzS * (kOzBM + kOzBN) * 16 +
                       256 * 8 * sizeof(double);
   // set once per process (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(
       oz_gemm_kernel<MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (attr != cudaSuccess) return attr;
-  oz_gemm_kernel<MODE, NS><<<grid, 256, smem, st>>>(M, Ma, N, Kp, k_split, PA, EA, PB, Np, EB, C,
-                                                    ldc);
+  oz_gemm_kernel<MODE, NS><<<grid, 256, smem, st>>>(M, Ma, a0, N, Kp, k_split, PA, EA, PB, Np, EB,
+                                                    C, ldc);
   note_launch();
   return cudaGetLastError();
 }
@@ -359,13 +409,13 @@ cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, in
   int* EB = EA + n;
   oz_row_exp_kernel<<<ceil_div((long long)n * 32, 256) < 16 * kSMs ? ceil_div((long long)n * 32, 256) : 16 * kSMs,
                       256, 0, st>>>(n, A, lda, K, EA); note_launch();
-  oz_split_rows_kernel<<<16 * kSMs, 256, 0, st>>>(n, A, lda, K, Kp, EA, PA); note_launch();
+  oz_split_rows_launch(st, n, A, lda, K, Kp, EA, PA);
   oz_split_cols_kernel<<<ceil_div((long long)nbp * 32, 256), 256, 0, st>>>(K, nb, B, ldb, Kp, nbp, EB,
                                                                             PB); note_launch();
   dim3 grid((unsigned)((long long)ceil_div(n, kOzBM) * (nbp / kOzBN)), 1, 1);
   const int ks = Kp / kOzBK;
-  if (subtract) return oz_launch_gemm<1>(st, grid, n, n, nb, Kp, ks, PA, EA, PB, nbp, EB, C, ldc);
-  return oz_launch_gemm<0>(st, grid, n, n, nb, Kp, ks, PA, EA, PB, nbp, EB, C, ldc);
+  if (subtract) return oz_launch_gemm<1>(st, grid, n, n, 0, nb, Kp, ks, PA, EA, PB, nbp, EB, C, ldc);
+  return oz_launch_gemm<0>(st, grid, n, n, 0, nb, Kp, ks, PA, EA, PB, nbp, EB, C, ldc);
 }
 
 // ---------------- Gram products A^T B (reduction over the N rows) ----------------
@@ -393,32 +443,6 @@ __global__ void __launch_bounds__(256) oz_col_exp_kernel(int n, const double* __
 
 int oz_chunks(int Np) { return ceil_div(Np, kOzChunk); }
 
-// Transposed slices of X (N x w): planes S x wp x Np, plane[s][c][r] = digit s of x_rc.
-// 32 x 32 tiles through shared memory so that reads and writes are both contiguous.
-__global__ void oz_split_cols_t_kernel(int n, const double* __restrict__ X, int ldx, int w, int Np,
-                                       int wp, const int* __restrict__ E,
-                                       __nv_bfloat16* __restrict__ P) {
-  __shared__ double tile[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
-  const int r0 = blockIdx.x * 32, cb = blockIdx.y * 32;
-  for (int i = ty; i < 32; i += 8) {
-    const int r = r0 + i, c = cb + tx;
-    tile[i][tx] = (r < n && c < w) ? X[(size_t)r * ldx + c] : 0.0;
-  }
-  __syncthreads();
-  const size_t plane = (size_t)wp * Np;
-  for (int i = ty; i < 32; i += 8) {
-    const int c = cb + i, r = r0 + tx;
-    if (c >= wp || r >= Np) continue;
-    const double a = tile[tx][i];
-    int d[kOzS];
-    oz_digits(oz_fixed(a, c < w ? E[(size_t)(r / kOzChunk) * wp + c] : 0), d);
-    const bool neg = a < 0.0;
-#pragma unroll
-    for (int s = 0; s < kOzS; ++s) P[s * plane + (size_t)c * Np + r] = oz_bf16(d[s], neg);
-  }
-}
-
 size_t ozaki_tn_work_bytes(int n, int ka, int kb) {
   const size_t Np = (size_t)round_up(n, kOzBK);
   const size_t kap = (size_t)round_up(ka, kOzBM), kbp = (size_t)round_up(kb, kOzBN);
@@ -429,7 +453,8 @@ size_t ozaki_tn_work_bytes(int n, int ka, int kb) {
 }
 
 cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, int ka,
-                            const double* B, int ldb, int kb, double* out, void* work) {
+                            const double* B, int ldb, int kb, double* out, void* work,
+                            int* tc_err) {
   if (n <= 0 || ka <= 0 || kb <= 0) return cudaSuccess;
   const int Np = round_up(n, kOzBK);
   const int kap = round_up(ka, kOzBM), kbp = round_up(kb, kOzBN);
@@ -442,12 +467,12 @@ cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, in
   int* Eend = EB + (size_t)kbp * nch;
   double* partial = reinterpret_cast<double*>(
       reinterpret_cast<char*>(Eend) + (256 - (reinterpret_cast<uintptr_t>(Eend) & 255)));
-  oz_col_exp_kernel<<<dim3(nch, ceil_div(ka, 32)), 256, 0, st>>>(n, A, lda, ka, kap, 0, EA); note_launch();
-  oz_col_exp_kernel<<<dim3(nch, ceil_div(kb, 32)), 256, 0, st>>>(n, B, ldb, kb, kbp, 0, EB); note_launch();
-  dim3 ga(ceil_div(Np, 32), ceil_div(kap, 32));
-  oz_split_cols_t_kernel<<<ga, 256, 0, st>>>(n, A, lda, ka, Np, kap, EA, PA); note_launch();
-  dim3 gb(ceil_div(Np, 32), ceil_div(kbp, 32));
-  oz_split_cols_t_kernel<<<gb, 256, 0, st>>>(n, B, ldb, kb, Np, kbp, EB, PB); note_launch();
+  cudaError_t e0 = oz_slice_cols_t(st, n, A, lda, ka, Np, kap, 0, PA, EA);
+  if (e0 != cudaSuccess) return e0;
+  e0 = oz_slice_cols_t(st, n, B, ldb, kb, Np, kbp, 0, PB, EB);
+  if (e0 != cudaSuccess) return e0;
+  if (tc_err != nullptr)   // tcgen05 products with tensor-memory level sums (tc05.cu)
+    return launch_tc_gram(st, Np, PA, EA, kap, 0, ka, PB, EB, kbp, kb, out, partial, kOzS, tc_err);
   // split the reduction so that the grid covers the GPU about twice
   const int tiles = (kap / kOzBM) * (kbp / kOzBN);
   const int nk = Np / kOzBK;
@@ -457,7 +482,7 @@ cudaError_t launch_ozaki_tn(cudaStream_t st, int n, const double* A, int lda, in
   nsplit = ceil_div(nk, k_split);
   dim3 grid(kap / kOzBM, kbp / kOzBN, nsplit);
   cudaError_t e =
-      oz_launch_gemm<2>(st, grid, ka, kap, kb, Np, k_split, PA, EA, PB, kbp, EB, partial, kb);
+      oz_launch_gemm<2>(st, grid, ka, kap, 0, kb, Np, k_split, PA, EA, PB, kbp, EB, partial, kb);
   if (e != cudaSuccess) return e;
   return launch_reduce_partials(st, partial, nsplit, ka * kb, out, 1.0);
 }
@@ -475,23 +500,21 @@ cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int 
   __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
   oz_row_exp_kernel<<<ceil_div((long long)n * 32, 256) < 16 * kSMs ? ceil_div((long long)n * 32, 256) : 16 * kSMs,
                       256, 0, st>>>(n, A, lda, K, E); note_launch();
-  oz_split_rows_kernel<<<16 * kSMs, 256, 0, st>>>(n, A, lda, K, Kp, E, P); note_launch();
+  oz_split_rows_launch(st, n, A, lda, K, Kp, E, P);
   return cudaGetLastError();
 }
 
-// Transposed column slices of A's w columns into rows [c0, c0 + w) of planes S x cap x Np,
-// chunk exponents into E[ch * cap + c0 .. + w) for every 1024-row chunk ch < oz_chunks(Np).
-// Rows of the planes outside [c0, c0 + w) are untouched.
-// Transposed slices of columns c_off.. of the planes (S x cap x Np, chunk exponents E): a 64-row
-// x 32-column tile of X staged column-major in shared memory; each lane splits two adjacent
-// rows of one column and stores both digits of a plane as one 4-byte word (a warp writes 128
-// contiguous bytes per plane).  Np is a multiple of 16 and the row even, so the word is aligned
-// and both rows lie in the same 1024-row exponent chunk.
+// Transposed column slices: columns [0, w) of X (N x w) become rows [c_off, c_off + w) of the
+// tiled planes with `cap` rows and Np values of k (the N rows of X, zero padded), with chunk
+// exponents E[ch * cap + c_off + c].  A 64-row x 32-column tile of X is staged in shared
+// memory; thread t splits 8 consecutive rows of one column and stores one 16-byte piece per
+// slice (consecutive threads: consecutive columns, so a warp writes 512 contiguous bytes).
+// Rows of the planes outside [c_off, c_off + w) are untouched.
 constexpr int kOzTRows = 64;
 
-__global__ void oz_split_cols_t_off_kernel(int n, const double* __restrict__ X, int ldx, int w, int Np,
-                                           int cap, int c_off, const int* __restrict__ E,
-                                           __nv_bfloat16* __restrict__ P) {
+__global__ void __launch_bounds__(256) oz_split_cols_t_off_kernel(
+    int n, const double* __restrict__ X, int ldx, int w, int Np, int cap, int c_off,
+    const int* __restrict__ E, __nv_bfloat16* __restrict__ P) {
   __shared__ double tile[32][kOzTRows + 1];   // [column][row]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 8 warps
   const int r0 = blockIdx.x * kOzTRows, cb = blockIdx.y * 32;
@@ -500,26 +523,26 @@ __global__ void oz_split_cols_t_off_kernel(int n, const double* __restrict__ X, 
     tile[lane][i] = (r < n && c < w) ? X[(size_t)r * ldx + c] : 0.0;
   }
   __syncthreads();
-  const size_t plane = (size_t)cap * Np;
-  const int r = r0 + 2 * lane;
-  for (int ci = warp; ci < 32; ci += 8) {
-    const int c = cb + ci;
-    if (c >= w) break;
-    if (r >= Np) continue;
-    const double a0 = tile[ci][2 * lane], a1 = tile[ci][2 * lane + 1];
-    const int e = E[(size_t)(r / kOzChunk) * cap + c_off + c];
+  const int c = cb + lane, g = warp;   // rows r0 + 8g .. r0 + 8g + 7
+  const int r = r0 + 8 * g;
+  if (c >= w || r >= Np) return;
+  const int e = E[(size_t)(r / kOzChunk) * cap + c_off + c];
+  uint32_t wd[kOzS][4];
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    const double a0 = tile[lane][8 * g + j], a1 = tile[lane][8 * g + j + 1];
     int d0[kOzS], d1[kOzS];
     oz_digits(oz_fixed(a0, e), d0);
     oz_digits(oz_fixed(a1, e), d1);
-    const bool n0 = a0 < 0.0, n1 = a1 < 0.0;
-    uint32_t* dst = reinterpret_cast<uint32_t*>(P + (size_t)(c_off + c) * Np + r);
 #pragma unroll
-    for (int s = 0; s < kOzS; ++s) {
-      const uint32_t lo = __bfloat16_as_ushort(oz_bf16(d0[s], n0));
-      const uint32_t hi = __bfloat16_as_ushort(oz_bf16(d1[s], n1));
-      dst[s * (plane / 2)] = lo | (hi << 16);
-    }
+    for (int s = 0; s < kOzS; ++s)
+      wd[s][j >> 1] = (uint32_t)__bfloat16_as_ushort(oz_bf16(d0[s], a0 < 0.0)) |
+                      ((uint32_t)__bfloat16_as_ushort(oz_bf16(d1[s], a1 < 0.0)) << 16);
   }
+#pragma unroll
+  for (int s = 0; s < kOzS; ++s)
+    *reinterpret_cast<uint4*>(P + oz_tix(s, (size_t)c_off + c, r, cap)) =
+        make_uint4(wd[s][0], wd[s][1], wd[s][2], wd[s][3]);
 }
 
 cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, int w, int Np, int cap,
@@ -533,17 +556,6 @@ cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, in
   return cudaGetLastError();
 }
 
-// zero the padding rows [from, to) of planes S x cap x Np (so a padded GEMM tile reads zeros)
-__global__ void oz_zero_rows_kernel(__nv_bfloat16* P, size_t plane, int Np, int from, int to) {
-  const long long total = (long long)(to - from) * Np;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total * kOzS;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(i / total);
-    const long long rem = i - (long long)s * total;
-    P[s * plane + (size_t)from * Np + rem] = __float2bfloat16_rn(0.f);
-  }
-}
-
 // out (ka x kb) = A^T B from transposed planes: rows [a0, a0 + ka) of PA (S x capA x Np,
 // chunk exponents EA, stride capA) and rows [0, kb) of PB (S x capB x Np, chunk exponents EB,
 // stride capB; capB >= round_up(kb, 32)).
@@ -551,7 +563,7 @@ cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const i
                                 int a0, int ka, const void* PB, const int* EB, int capB, int kb,
                                 double* out, double* partial, int slices) {
   if (ka <= 0 || kb <= 0) return cudaSuccess;
-  const __nv_bfloat16* pa = static_cast<const __nv_bfloat16*>(PA) + (size_t)a0 * Np;
+  const __nv_bfloat16* pa = static_cast<const __nv_bfloat16*>(PA);
   const __nv_bfloat16* pb = static_cast<const __nv_bfloat16*>(PB);
   const int mt = ceil_div(ka, kOzBM), nt = ceil_div(kb, kOzBN);
   const int tiles = mt * nt;
@@ -560,16 +572,16 @@ cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const i
   const int k_split = round_up(ceil_div(nk, nsplit), kOzFlush);   // chunk-aligned splits
   nsplit = ceil_div(nk, k_split);
   dim3 grid(mt, nt, nsplit);
-  // the planes of A are read through an offset base: their row count per plane stays capA
+  // rows a0 .. a0 + ka - 1 of A's planes (capA rows)
   cudaError_t e;
   if (slices == 4)
-    e = oz_launch_gemm<2, 4>(st, grid, ka, capA, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
+    e = oz_launch_gemm<2, 4>(st, grid, ka, capA, a0, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
                              partial, kb);
   else if (slices == 6)
-    e = oz_launch_gemm<2, 6>(st, grid, ka, capA, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
+    e = oz_launch_gemm<2, 6>(st, grid, ka, capA, a0, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
                              partial, kb);
   else if (slices == kOzS)
-    e = oz_launch_gemm<2>(st, grid, ka, capA, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
+    e = oz_launch_gemm<2>(st, grid, ka, capA, a0, kb, Np, k_split, pa, EA + a0, pb, capB, EB,
                           partial, kb);
   else
     return cudaErrorInvalidValue;
@@ -594,12 +606,12 @@ cudaError_t oz_nn_from_planes(cudaStream_t st, int n, int K, int Kp, const void*
   // the product C = A B may use 6 (operands to 36 bits)
   if (subtract) {
     if (slices != kOzS) return cudaErrorInvalidValue;
-    return oz_launch_gemm<1>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
+    return oz_launch_gemm<1>(st, grid, n, n, 0, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
   }
   if (slices == 6)
-    return oz_launch_gemm<0, 6>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
+    return oz_launch_gemm<0, 6>(st, grid, n, n, 0, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
   if (slices != kOzS) return cudaErrorInvalidValue;
-  return oz_launch_gemm<0>(st, grid, n, n, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
+  return oz_launch_gemm<0>(st, grid, n, n, 0, nb, Kp, Kp / kOzBK, pa, EA, PB, nbp, EB, C, ldc);
 }
 
 cudaError_t oz_nn_from_planes_tc(cudaStream_t st, int n, int K, int Kp, const void* PA,

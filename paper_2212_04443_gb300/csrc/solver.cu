@@ -287,6 +287,18 @@ bchdav_status run_filter_mixed(bchdav_handle h, const bchdav_csr* A, const float
   return BCHDAV_OK;
 }
 
+// Gram product A^T B of cached transposed planes (Steps 6 and 8): on tcgen05 with tensor-memory
+// level sums (dense_path 0) or on warp-level mma (dense_path 2); partial sums in oz_part.
+cudaError_t gram_planes(bchdav_handle h, int dense_path, int Np, const void* PA, const int* EA,
+                        int capA, int a0, int ka, const void* PB, const int* EB, int capB, int kb,
+                        double* out, int slices = 8) {
+  if (dense_path == 0)
+    return launch_tc_gram(h->stream, Np, PA, EA, capA, a0, ka, PB, EB, capB, kb, out,
+                          h->oz_part.as<double>(), slices, h->tc_err.as<int>());
+  return oz_gram_from_planes(h->stream, Np, PA, EA, capA, a0, ka, PB, EB, capB, kb, out,
+                             h->oz_part.as<double>(), slices);
+}
+
 // ---------------- Step 6 ----------------
 // Where the cached slices of V live: column planes of V (S x capV x Np, exponents after them) in
 // oz_vt and row planes (S x n x KpCap, exponents after them) in oz_vr.  Both are sized for the
@@ -349,6 +361,7 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   // and serve both passes and every retry; X is sliced by columns for each Gram product
   if (vt_valid) *vt_valid = 0;
   const bool tc = (dense_path == 0 || dense_path == 2) && ozaki_nn_supported(std::max(k, 1));
+  if (tc && dense_path == 0) BCHDAV_TRY(h->ensure(h->tc_err, sizeof(int)));
   const OzLayout L = oz_layout(n, std::max(k, cap_cols));
   const int Np = L.Np, capV = L.capV, capX = oz_pad_cols(b);
   const int Kp = oz_pad_k(std::max(k, 1));
@@ -377,9 +390,9 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
           // both passes float64-accurate (a first pass from truncated slices measurably loosened
           // the orthogonality on graphs with hub rows)
           HCUDA(oz_slice_cols_t(st, n, X, ldx, b, Np, capX, 0, h->oz_xt.p, Ext));
-          HCUDA(oz_gram_from_planes(st, Np, h->oz_vt.p, Evt, capV, 0, k, h->oz_xt.p, Ext, capX, b,
-                                    Gd, h->oz_part.as<double>()));
-          if (dense_path == 2)
+          HCUDA(gram_planes(h, dense_path, Np, h->oz_vt.p, Evt, capV, 0, k, h->oz_xt.p, Ext, capX,
+                            b, Gd));
+          if (dense_path == 0)
             HCUDA(oz_nn_from_planes_tc(st, n, k, Kp, h->oz_vr.p, Evr, Gd, b, b, X, ldx, true,
                                        h->oz_bw.p, 8, h->tc_err.as<int>()));
           else
@@ -600,8 +613,18 @@ bchdav_status bchdav_orthonormalize(bchdav_handle h, int32_t n, const double* V,
     return BCHDAV_ERR_ARG;
   }
   int nr = 0;
+  BCHDAV_TRY(h->ensure(h->tc_err, sizeof(int)));
+  HCUDA(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), h->stream));
   bchdav_status s = run_orth(h, n, V, ldv, k, X, ldx, b, seed, tau_dep, rep_counter, &nr);
   if (n_replaced) *n_replaced = nr;
+  if (s != BCHDAV_OK) return s;
+  int flag = 0;
+  HCUDA(cudaMemcpyAsync(&flag, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  HCUDA(cudaStreamSynchronize(h->stream));
+  if (flag) {
+    h->set_error(BCHDAV_ERR_TIMEOUT, "orthonormalize: a tensor-core wait expired");
+    return BCHDAV_ERR_TIMEOUT;
+  }
   return s;
 }
 
@@ -616,7 +639,22 @@ bchdav_status bchdav_gram(bchdav_handle h, int32_t n, const double* A, int32_t l
   }
   if (dense_path != 1) {
     BCHDAV_TRY(h->ensure(h->oz, ozaki_tn_work_bytes(n, ka, kb)));
-    HCUDA(launch_ozaki_tn(h->stream, n, A, lda, ka, B, ldb, kb, out, h->oz.p));
+    int* err = nullptr;
+    if (dense_path == 0) {
+      BCHDAV_TRY(h->ensure(h->tc_err, sizeof(int)));
+      HCUDA(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), h->stream));
+      err = h->tc_err.as<int>();
+    }
+    HCUDA(launch_ozaki_tn(h->stream, n, A, lda, ka, B, ldb, kb, out, h->oz.p, err));
+    if (err) {
+      int flag = 0;
+      HCUDA(cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      HCUDA(cudaStreamSynchronize(h->stream));
+      if (flag) {
+        h->set_error(BCHDAV_ERR_TIMEOUT, "gram: a tensor-core wait expired");
+        return BCHDAV_ERR_TIMEOUT;
+      }
+    }
   } else {
     const int chunks = gemm_tn_chunks(n);
     BCHDAV_TRY(h->ensure(h->part, (size_t)chunks * ka * kb * sizeof(double)));
@@ -634,7 +672,7 @@ bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, 
     h->set_error(BCHDAV_ERR_ARG, "rotate: bad arguments");
     return BCHDAV_ERR_ARG;
   }
-  if (dense_path == 2 && ozaki_nn_supported(k)) {
+  if (dense_path == 0 && ozaki_nn_supported(k)) {
     // tcgen05 slice product from V's row planes (in place: the planes hold all of V)
     const int Kp = oz_pad_k(k);
     BCHDAV_TRY(h->ensure(h->oz, oz_planes_bytes(n, Kp) + (size_t)n * sizeof(int) + 256));
@@ -652,7 +690,7 @@ bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, 
       h->set_error(BCHDAV_ERR_TIMEOUT, "rotate: a tensor-core wait expired");
       return BCHDAV_ERR_TIMEOUT;
     }
-  } else if (dense_path == 0 && ozaki_nn_supported(k)) {
+  } else if (dense_path == 2 && ozaki_nn_supported(k)) {
     BCHDAV_TRY(h->ensure(h->oz, ozaki_nn_work_bytes(n, k, nb)));
     HCUDA(launch_ozaki_nn(h->stream, n, V, ldv, k, Y, ld_y, nb, V, ldv, false, h->oz.p));
   } else {
@@ -906,8 +944,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       HCUDA(oz_slice_cols_t(st, N, V + c_from, ldv, k_sub - c_from, OL.Np, OL.capV, c_from,
                             h->oz_vt.p, Evt));
       HCUDA(oz_slice_cols_t(st, N, W, ldb, b, OL.Np, capX, 0, h->oz_xt.p, Ext));
-      HCUDA(oz_gram_from_planes(st, OL.Np, h->oz_vt.p, Evt, OL.capV, k_c, k_act, h->oz_xt.p, Ext,
-                                capX, b, h->G.as<double>(), h->oz_part.as<double>()));
+      HCUDA(gram_planes(h, opts.dense_path, OL.Np, h->oz_vt.p, Evt, OL.capV, k_c, k_act,
+                        h->oz_xt.p, Ext, capX, b, h->G.as<double>()));
     } else {
       HCUDA(launch_gemm_tn_partial(st, N, V + k_c, ldv, k_act, W, ldb, b, h->part.as<double>(),
                                    chunks));
@@ -937,7 +975,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       int* Evr = reinterpret_cast<int*>(h->oz_vr.as<char>() + OL.vr_planes);
       const int Kp = oz_pad_k(k_old);
       HCUDA(oz_slice_rows(st, N, V + k_c, ldv, k_old, Kp, h->oz_vr.p, Evr));
-      if (opts.dense_path == 2)
+      if (opts.dense_path == 0)
         HCUDA(oz_nn_from_planes_tc(st, N, k_old, Kp, h->oz_vr.p, Evr, Ym, act_max, k_act, V + k_c,
                                    ldv, false, h->oz_bw.p, slices_rr, h->tc_err.as<int>()));
       else
@@ -1109,7 +1147,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   HCUDA(cudaStreamSynchronize(st));
   collect();
   tm_total.collect();
-  if (opts.dense_path == 2) {
+  if (opts.dense_path == 0) {
     int flag = 0;
     HCUDA(cudaMemcpy(&flag, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {

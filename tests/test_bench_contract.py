@@ -41,3 +41,18 @@ def test_bench_scores_match_the_oracle():
         assert ari == pytest.approx(cluster.adjusted_rand_index(a, b), abs=1e-12)
         assert nmi == pytest.approx(cluster.normalized_mutual_info(a, b), abs=1e-12)
     assert partition_scores([0, 0, 1, 1], [0, 0, 1, 2])[0] == pytest.approx(4 / 7)
+
+
+def test_filter_model_bytes_follow_the_scope_table():
+    """Compulsory filter bytes: per step 4 (N + 1) + nnz (4 + s) + 3 N b s, the first step of a
+    filter 2 N b s; the 1M-node SBM (nnz 18,988,714, b = 20, float32) moves 395.9 MB per full
+    step and 315.9 MB in its first."""
+    sys.path.insert(0, ROOT)
+    from bench import filter_model_bytes
+    n, nnz, b = 1_000_000, 18_988_714, 20
+    one = filter_model_bytes(n, nnz, b, 1, 1, 4.0)
+    two = filter_model_bytes(n, nnz, b, 2, 1, 4.0)
+    assert one == pytest.approx(4 * (n + 1) + nnz * 8 + 2 * n * b * 4)
+    assert two - one == pytest.approx(4 * (n + 1) + nnz * 8 + 3 * n * b * 4)
+    assert round((two - one) / 1e6, 1) == 395.9 and round(one / 1e6, 1) == 315.9
+    assert filter_model_bytes(n, nnz, b, 15, 16, 4.0) == pytest.approx(16 * (one + 14 * (two - one)))

@@ -216,8 +216,8 @@ def test_deterministic_repeat(H):
 
 
 def test_dense_paths_agree(H):
-    """Tensor-core split products (warp-level mma, or tcgen05 for the row-operand products) and
-    plain float64 FMA kernels give the same solve."""
+    """The float64-accurate slice products on tcgen05 (path 0, the default) and on warp-level
+    mma (path 2), and plain float64 FMA kernels (path 1) give the same solve."""
     g = synth.sbm_edges(20000, 20, d_in=14, d_out=2, seed=13)
     a = gpu_solve(H, g, 20, 10, 13, 50, dense_path=0)
     b = gpu_solve(H, g, 20, 10, 13, 50, dense_path=1)
@@ -229,8 +229,9 @@ def test_dense_paths_agree(H):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_tcgen05_path_matches_oracle(H, prec):
-    """dense_path 2 on the oracle-parity case and on a hub graph, both precisions."""
+def test_warp_mma_path_matches_oracle(H, prec):
+    """dense_path 2 (the slice products on the legacy warp-level mma) on the oracle-parity case
+    and on a hub graph, both precisions (every other solve test runs the default tcgen05 path)."""
     g = synth.sbm_edges(20000, 20, d_in=14, d_out=2, seed=13)
     ev, V, info, hist = gpu_solve(H, g, 20, 10, 13, 50, precision=prec, dense_path=2)
     L, r = oracle_solve(g, 20, 10, 13, 50)

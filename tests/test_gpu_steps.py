@@ -247,8 +247,8 @@ def test_eigh_diagonal_plus_border(H):
                                     (130001, 96, 70)])
 @pytest.mark.parametrize("path", [0, 1, 2])
 def test_rotate_matches_float64(H, n, k, nb, path):
-    """Step 11 product V(:, :nb) = V(:, :k) Y: tensor-core split on warp-level mma (path 0) or
-    on tcgen05 with tensor-memory accumulators (path 2), and float64 FMA (path 1)."""
+    """Step 11 product V(:, :nb) = V(:, :k) Y: float64-accurate slice product on tcgen05 with
+    tensor-memory level sums (path 0) or on warp-level mma (path 2), and float64 FMA (path 1)."""
     import torch
     rng = synth.rng(n + k)
     V = rng.standard_normal((n, k)) / np.sqrt(n)
@@ -268,10 +268,13 @@ def test_rotate_matches_float64(H, n, k, nb, path):
     assert np.abs(out[3, :nb]).max() == 0.0
 
 
-@pytest.mark.parametrize("n,ka,kb", [(1000003, 300, 20), (5000, 77, 45), (3001, 1, 1), (70000, 340, 20)])
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("n,ka,kb", [(1000003, 300, 20), (5000, 77, 45), (3001, 1, 1), (70000, 340, 20),
+                                     (200000, 130, 64), (1037, 129, 33)])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_gram_matches_float64(H, n, ka, kb, path):
-    """Steps 6/8 product A^T B with a reduction over n rows (pieces of 1024 rows when split)."""
+    """Steps 6/8 product A^T B with a reduction over n rows (pieces of 1024 rows when split):
+    tcgen05 with tensor-memory level sums and an integer fold (path 0), float64 FMA (path 1),
+    warp-level mma (path 2); ragged tiles in every dimension."""
     import torch
     rng = synth.rng(n + ka)
     A = rng.standard_normal((n, ka)) / np.sqrt(n)
@@ -284,7 +287,7 @@ def test_gram_matches_float64(H, n, ka, kb, path):
     assert np.all(np.abs(out - ref) <= bound + 1e-13 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_gram_per_chunk_precision_with_hub_entries(H, path):
     """A^T B where one row dwarfs the rest of its column (a hub vertex).  The split scales each
     1024-row chunk by its own column exponent: with the hub alone in its chunk, the other rows
@@ -324,9 +327,15 @@ def test_tcgen05_wait_timeout_reports_and_recovers(H, monkeypatch):
     Yd = torch.from_numpy(Y).cuda()
     monkeypatch.setenv("BCHDAV_TEST_EXPIRE_TC_WAIT", "1")
     with pytest.raises(P.BchdavError) as ei:
-        H.rotate(torch.from_numpy(V.copy()).cuda(), Yd, nb, dense_path=2)
+        H.rotate(torch.from_numpy(V.copy()).cuda(), Yd, nb, dense_path=0)
+    assert ei.value.status == -6
+    A = torch.from_numpy(V).cuda()
+    with pytest.raises(P.BchdavError) as ei:
+        H.gram(A, A[:, :7], dense_path=0)
     assert ei.value.status == -6
     monkeypatch.delenv("BCHDAV_TEST_EXPIRE_TC_WAIT")
     Vd = torch.from_numpy(V.copy()).cuda()
-    H.rotate(Vd, Yd, nb, dense_path=2)
+    H.rotate(Vd, Yd, nb, dense_path=0)
     assert np.abs(to_np(Vd)[:, :nb] - V @ Y).max() <= 1e-13 * np.abs(V @ Y).max()
+    G = to_np(H.gram(A, A[:, :7].contiguous(), dense_path=0))
+    assert np.abs(G - V.T @ V[:, :7]).max() <= 1e-13
