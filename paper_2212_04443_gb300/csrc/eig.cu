@@ -255,8 +255,9 @@ cudaError_t launch_eigh(cudaStream_t st, int n, const double* H, int ldh, double
 // computes the same rotations of a round from the current diagonal and pair
 // entries (Rutishauser's formulas), then the grid updates the disjoint 2x2
 // blocks of A <- J^T A J and the column pairs of V <- V J, and one grid barrier
-// ends the round.  Sweeps repeat until the off-diagonal mass is below
-// (eps * ||A||_F)^2.  Eigenvalues come out on the diagonal, sorted ascending
+// (about 1.3 us on GB300, whatever the grid) ends the round.  Sweeps repeat
+// until the off-diagonal mass is below (eps * ||A||_F)^2 or a sweep finds
+// nothing to rotate.  Eigenvalues come out on the diagonal, sorted ascending
 // at the end with their columns of V.
 
 constexpr int kJacThreads = 256;
@@ -265,7 +266,9 @@ constexpr int kJacMaxSweeps = 40;
 
 struct JacLayout {
   double *A, *V, *red, *ang;
-  int* status;
+  int* status;               // 0 converged, 1 sweep limit, 2 a grid barrier gave up
+  unsigned* bar;             // arrivals at the grid barrier (zeroed before each launch)
+  int* where;                // the barrier that gave up: sweep * 4096 + round (debug)
 };
 
 __host__ __device__ inline JacLayout jac_layout(double* w, int n) {
@@ -276,6 +279,8 @@ __host__ __device__ inline JacLayout jac_layout(double* w, int n) {
   L.red = L.V + (size_t)np * np;   // [2][grid] partial sums
   L.ang = L.red + 2 * 4 * kSMs;     // [2][np / 2][3] angle inputs (a_pp, a_qq, a_pq) by round parity
   L.status = reinterpret_cast<int*>(L.ang + 3 * (size_t)np + 8);
+  L.bar = reinterpret_cast<unsigned*>(L.status + 2);
+  L.where = L.status + 4;
   return L;
 }
 
@@ -319,14 +324,55 @@ __device__ __forceinline__ void jac_note_next(double* __restrict__ ang, int x, i
   }
 }
 
+// A is kept in its upper triangle only (entry (i, j) at min(i, j) * np + max(i, j)): a round
+// updates the 2x2 blocks (K, L) with K <= L, half of the float64 work of the full matrix.
+//
+// A rotation whose pair entry is negligible, a_pq^2 <= eps^2 |a_pp a_qq| (it changes the
+// eigenvalues by O(eps) relative and the eigenvectors by O(eps / relative gap)), is not applied.
+// Every CTA computes every angle of a round, so all of them see the same decisions: a round
+// without a rotation is skipped by all (no update, no barrier), and a sweep without a rotation
+// ends the iteration (A is diagonal to working accuracy), as does the off-diagonal mass test.
+// After a skipped round the next round reads its angle inputs from A itself, so before it
+// updates A it waits at a barrier until every CTA has read them.
+// Grid barrier of the cooperative launch with a bounded wait: thread 0 of each CTA adds its
+// arrival and polls the count until every CTA of this barrier instance has arrived; after
+// kJacSpin polls it gives up, and the CTA stops (status 2) instead of waiting forever.  Reads of
+// data other CTAs wrote go through L2 (__ldcg), so nothing stale is served from L1.
+constexpr long long kJacSpin = 1LL << 25;
+
+__device__ __forceinline__ bool jac_barrier(unsigned* bar, unsigned target, int* s_abort) {
+  __syncthreads();
+  if (threadIdx.x == 0 && !*s_abort) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    long long i = 0;
+    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+      if (++i > kJacSpin) {
+        *s_abort = 1;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return !*s_abort;
+}
+
+__device__ __forceinline__ int jac_ut(int i, int j, int np) {
+  return i < j ? i * np + j : j * np + i;
+}
+
 __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const double* __restrict__ H,
                                                                   int ldh, double* __restrict__ work,
                                                                   double* __restrict__ Dout,
                                                                   double* __restrict__ Y, int ldy) {
-  cg::grid_group grid = cg::this_grid();
   const int np = n + (n & 1);   // an odd n gets a dummy index n that is never rotated
   const int half = np / 2;
   JacLayout L = jac_layout(work, n);
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) s_abort = 0;
+  unsigned bar_target = 0;
+  int where = -1;
   extern __shared__ double sj[];
   double* cs = sj;            // half
   double* sn = sj + half;     // half
@@ -341,7 +387,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
   const long long gstride = (long long)gridDim.x * kJacThreads;
   double* A = L.A;
   double* V = L.V;
-  // A = H (symmetric, upper triangle read), padded row/column zero; V = I
+  // A = H (upper triangle read), padded row/column zero; V = I
   for (long long idx = gtid; idx < (long long)np * np; idx += gstride) {
     int i = (int)(idx / np), j = (int)(idx - (long long)i * np);
     double a = 0.0;
@@ -349,44 +395,52 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
     A[idx] = a;
     V[idx] = (i == j) ? 1.0 : 0.0;
   }
-  // angle inputs of round 0, straight from H
-  for (long long k = gtid; k < half; k += gstride) {
-    int p = jac_player((int)k, 0, np), q = jac_player(np - 1 - (int)k, 0, np);
-    if (p > q) {
-      const int x = p;
-      p = q;
-      q = x;
-    }
-    auto h = [&](int i, int j) {
-      return (i < n && j < n) ? ((i <= j) ? H[(size_t)i * ldh + j] : H[(size_t)j * ldh + i]) : 0.0;
-    };
-    L.ang[3 * k] = h(p, p);
-    L.ang[3 * k + 1] = h(q, q);
-    L.ang[3 * k + 2] = h(p, q);
-  }
   // ||A||_F^2 for the stopping threshold
   double loc = 0.0;
   for (long long idx = gtid; idx < (long long)np * np; idx += gstride) loc = fma(A[idx], A[idx], loc);
   double tot = block_sum(loc, s_red);
   if (t == 0) L.red[blockIdx.x] = tot;
-  grid.sync();
+  bar_target += gridDim.x;
+  jac_barrier(L.bar, bar_target, &s_abort);
   if (t == 0) {
     double sacc = 0.0;
-    for (int g = 0; g < (int)gridDim.x; ++g) sacc += L.red[g];
+    for (int g = 0; g < (int)gridDim.x; ++g) sacc += __ldcg(L.red + g);
     s_red[32] = sacc;
   }
   __syncthreads();
   const double eps = 2.220446049250313e-16;
   const double thresh = eps * eps * s_red[32];
   int status = 1;
-  for (int sweep = 0; sweep < kJacMaxSweeps; ++sweep) {
-    for (int r = 0; r < np - 1; ++r) {
-      const int rbuf = (int)(((long long)sweep * (np - 1) + r) & 1);   // angle inputs read now
+  // where the angle inputs of the next round are: A itself (after a skipped round, and at the
+  // start), or the slots of buffer rb written by the round before
+  bool from_A = true;
+  int rb = 0;
+  const long long nblk = (long long)half * (half + 1) / 2;   // blocks K <= L
+  const long long nitems = nblk + (long long)np * half;
+  for (int sweep = 0; sweep < kJacMaxSweeps && !s_abort; ++sweep) {
+    bool sweep_rotated = false;
+    for (int r = 0; r < np - 1 && !s_abort; ++r) {
+      const int wb = from_A ? rb : rb ^ 1;   // buffer this round's notes go to
+      // block (K, L), K <= L, of item idx < nblk (L-major)
+      auto block_of = [&](long long idx, int& K, int& Lb) {
+        int l = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+        while ((long long)l * (l + 1) / 2 > idx) --l;
+        while ((long long)(l + 1) * (l + 2) / 2 <= idx) ++l;
+        Lb = l;
+        K = (int)(idx - (long long)l * (l + 1) / 2);
+      };
+      auto ordered_pair = [&](int k, int& p, int& q) {
+        p = jac_player(k, r, np);
+        q = jac_player(np - 1 - k, r, np);
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+      };
       // The pairs of round r are fixed by r alone, so each thread first loads the entries its
       // (at most kJacPre) items will rotate, then the angles are computed while those loads
       // are in flight; the arithmetic is that of one rotation at a time per entry.
-      const long long nblk = (long long)half * half;
-      const long long nitems = nblk + (long long)np * half;
       double pre[kJacPre][4];
       int ppre[kJacPre][4];
 #pragma unroll
@@ -395,38 +449,34 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
         ppre[u][0] = -1;
         if (idx >= nitems) continue;
         if (idx < nblk) {
-          const int K = (int)(idx / half), Lb = (int)(idx - (long long)K * half);
-          int p1 = jac_player(K, r, np), q1 = jac_player(np - 1 - K, r, np);
-          int p2 = jac_player(Lb, r, np), q2 = jac_player(np - 1 - Lb, r, np);
-          if (p1 > q1) { const int x = p1; p1 = q1; q1 = x; }
-          if (p2 > q2) { const int x = p2; p2 = q2; q2 = x; }
-          ppre[u][0] = (int)(p1 * np + p2);
-          ppre[u][1] = (int)(p1 * np + q2);
-          ppre[u][2] = (int)(q1 * np + p2);
-          ppre[u][3] = (int)(q1 * np + q2);
-          pre[u][0] = A[ppre[u][0]];
-          pre[u][1] = A[ppre[u][1]];
-          pre[u][2] = A[ppre[u][2]];
-          pre[u][3] = A[ppre[u][3]];
+          int K, Lb, p1, q1, p2, q2;
+          block_of(idx, K, Lb);
+          ordered_pair(K, p1, q1);
+          ordered_pair(Lb, p2, q2);
+          ppre[u][0] = jac_ut(p1, p2, np);
+          ppre[u][1] = jac_ut(p1, q2, np);
+          ppre[u][2] = jac_ut(q1, p2, np);
+          ppre[u][3] = jac_ut(q1, q2, np);
+          pre[u][0] = __ldcg(A + ppre[u][0]);
+          pre[u][1] = __ldcg(A + ppre[u][1]);
+          pre[u][2] = __ldcg(A + ppre[u][2]);
+          pre[u][3] = __ldcg(A + ppre[u][3]);
         } else {
           const long long j = idx - nblk;
           const int row = (int)(j / half), K = (int)(j - (long long)row * half);
-          int p = jac_player(K, r, np), q = jac_player(np - 1 - K, r, np);
-          if (p > q) { const int x = p; p = q; q = x; }
+          int p, q;
+          ordered_pair(K, p, q);
           ppre[u][0] = (int)(row * np + p);
           ppre[u][1] = (int)(row * np + q);
-          pre[u][0] = V[ppre[u][0]];
-          pre[u][1] = V[ppre[u][1]];
+          pre[u][0] = __ldcg(V + ppre[u][0]);
+          pre[u][1] = __ldcg(V + ppre[u][1]);
         }
       }
       // rotations of this round, computed identically by every CTA
+      int mine = 0;
       for (int k = t; k < half; k += kJacThreads) {
-        int p = jac_player(k, r, np), q = jac_player(np - 1 - k, r, np);
-        if (p > q) {
-          int tmp = p;
-          p = q;
-          q = tmp;
-        }
+        int p, q;
+        ordered_pair(k, p, q);
         pp[k] = p;
         qq[k] = q;
         {
@@ -437,34 +487,57 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
         }
         double c = 1.0, s = 0.0;
         if (q < n) {
-          const double* in = L.ang + (size_t)rbuf * 3 * half + 3 * k;
-          const double apq = in[2];
-          if (apq != 0.0) {
-            const double app = in[0], aqq = in[1];
+          double app, aqq, apq;
+          if (from_A) {
+            app = __ldcg(A + (size_t)p * np + p);
+            aqq = __ldcg(A + (size_t)q * np + q);
+            apq = __ldcg(A + (size_t)p * np + q);
+          } else {
+            const double* in = L.ang + (size_t)rb * 3 * half + 3 * k;
+            app = __ldcg(in);
+            aqq = __ldcg(in + 1);
+            apq = __ldcg(in + 2);
+          }
+          if (apq != 0.0 && apq * apq > eps * eps * fabs(app * aqq)) {
             const double theta = (aqq - app) / (2.0 * apq);
             const double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
             c = 1.0 / sqrt(fma(tt, tt, 1.0));
             s = tt * c;
+            mine = 1;
           }
         }
         cs[k] = c;
         sn[k] = s;
       }
-      __syncthreads();
-      // A <- J^T A J on the 2x2 blocks (K, L); V <- V J on the column pairs
+      if (!__syncthreads_or(mine)) {   // the same in every CTA: nothing rotates this round
+        from_A = true;
+        continue;
+      }
+      sweep_rotated = true;
+      // A round that read its angle inputs from A must not update A before every CTA has read
+      // them (a faster CTA would otherwise overwrite entries a slower one has yet to read)
+      if (from_A) {
+        bar_target += gridDim.x;
+        if (!jac_barrier(L.bar, bar_target, &s_abort)) {
+          where = sweep * 4096 + r;
+          break;
+        }
+      }
+      // A <- J^T A J on the upper-triangle 2x2 blocks (K, L); V <- V J on the column pairs
       auto apply = [&](long long idx, double (&x)[4], const int (&off)[4], bool loaded) {
         if (idx < nblk) {
-          const int K = (int)(idx / half), Lb = (int)(idx - (long long)K * half);
+          int K, Lb;
+          block_of(idx, K, Lb);
           const double c1 = cs[K], s1 = sn[K], c2 = cs[Lb], s2 = sn[Lb];
           const int p1 = pp[K], q1 = qq[K], p2 = pp[Lb], q2 = qq[Lb];
           int o[4] = {off[0], off[1], off[2], off[3]};
           if (!loaded) {
-            o[0] = p1 * np + p2;
-            o[1] = p1 * np + q2;
-            o[2] = q1 * np + p2;
-            o[3] = q1 * np + q2;
+            o[0] = jac_ut(p1, p2, np);
+            o[1] = jac_ut(p1, q2, np);
+            o[2] = jac_ut(q1, p2, np);
+            o[3] = jac_ut(q1, q2, np);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) x[e] = A[o[e]];
+            for (int e = 0; e < 4; ++e) x[e] = __ldcg(A + o[e]);
           }
           double z[4] = {x[0], x[1], x[2], x[3]};
           if (!(s1 == 0.0 && s2 == 0.0)) {
@@ -483,10 +556,15 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
           }
           {
             const int np1 = npp[K], nq1 = nqq[K], np2 = npp[Lb], nq2 = nqq[Lb];
-            jac_note_next(L.ang, p1, p2, np1, np2, z[0], r, np, rbuf ^ 1);
-            jac_note_next(L.ang, p1, q2, np1, nq2, z[1], r, np, rbuf ^ 1);
-            jac_note_next(L.ang, q1, p2, nq1, np2, z[2], r, np, rbuf ^ 1);
-            jac_note_next(L.ang, q1, q2, nq1, nq2, z[3], r, np, rbuf ^ 1);
+            const int xs[4] = {p1, p1, q1, q1}, ys[4] = {p2, q2, p2, q2};
+            const int pxs[4] = {np1, np1, nq1, nq1}, pys[4] = {np2, nq2, np2, nq2};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (xs[e] <= ys[e])
+                jac_note_next(L.ang, xs[e], ys[e], pxs[e], pys[e], z[e], r, np, wb);
+              else
+                jac_note_next(L.ang, ys[e], xs[e], pys[e], pxs[e], z[e], r, np, wb);
+            }
           }
         } else {
           const long long j = idx - nblk;
@@ -497,8 +575,8 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
           if (!loaded) {
             o0 = row * np + pp[K];
             o1 = row * np + qq[K];
-            x[0] = V[o0];
-            x[1] = V[o1];
+            x[0] = __ldcg(V + o0);
+            x[1] = __ldcg(V + o1);
           }
           const double xp = x[0], xq = x[1];
           V[o0] = c * xp - s * xq;
@@ -515,20 +593,39 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
         const int off[4] = {0, 0, 0, 0};
         apply(idx, x, off, false);
       }
-      grid.sync();
+      bar_target += gridDim.x;
+      if (!jac_barrier(L.bar, bar_target, &s_abort)) {
+        where = sweep * 4096 + r;
+        break;
+      }
+      from_A = false;
+      rb = wb;
     }
-    // off-diagonal mass after the sweep
+    if (s_abort) break;
+    if (!sweep_rotated) {   // the same in every CTA
+      status = 0;
+      break;
+    }
+    // off-diagonal mass after the sweep (upper triangle, counted twice)
     loc = 0.0;
     for (long long idx = gtid; idx < (long long)np * np; idx += gstride) {
       int i = (int)(idx / np), j = (int)(idx - (long long)i * np);
-      if (i != j) loc = fma(A[idx], A[idx], loc);
+      if (i < j) {
+        const double a = __ldcg(A + idx);
+        loc = fma(2.0 * a, a, loc);
+      }
     }
     tot = block_sum(loc, s_red);
     if (t == 0) L.red[((sweep + 1) & 1) * 4 * kSMs + blockIdx.x] = tot;
-    grid.sync();
+    bar_target += gridDim.x;
+    if (!jac_barrier(L.bar, bar_target, &s_abort)) {
+      where = sweep * 4096 + 4095;
+      break;
+    }
     if (t == 0) {
       double sacc = 0.0;
-      for (int g = 0; g < (int)gridDim.x; ++g) sacc += L.red[((sweep + 1) & 1) * 4 * kSMs + g];
+      for (int g = 0; g < (int)gridDim.x; ++g)
+        sacc += __ldcg(L.red + ((sweep + 1) & 1) * 4 * kSMs + g);
       s_flag = (sacc <= thresh) ? 1 : 0;
     }
     __syncthreads();
@@ -537,18 +634,26 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
       break;
     }
   }
+  if (s_abort) {
+    // a barrier gave up: report it and write nothing (the other CTAs stop at theirs)
+    if (threadIdx.x == 0) {
+      atomicExch(L.status, 2);
+      if (where >= 0) atomicExch(L.where, where);
+    }
+    return;
+  }
   // ascending order of the diagonal (stable ranks); every CTA writes a share of the output
   for (int i = (int)gtid; i < n; i += (int)gstride) {
-    const double di = A[(size_t)i * np + i];
+    const double di = __ldcg(A + (size_t)i * np + i);
     int rk = 0;
     for (int j = 0; j < n; ++j) {
-      const double dj = A[(size_t)j * np + j];
+      const double dj = __ldcg(A + (size_t)j * np + j);
       rk += (dj < di) || (dj == di && j < i);
     }
     Dout[rk] = di;
-    for (int row = 0; row < n; ++row) Y[(size_t)row * ldy + rk] = V[(size_t)row * np + i];
+    for (int row = 0; row < n; ++row) Y[(size_t)row * ldy + rk] = __ldcg(V + (size_t)row * np + i);
   }
-  if (gtid == 0) *L.status = status;
+  if (gtid == 0) atomicMax(L.status, status);
 }
 
 cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
@@ -569,20 +674,29 @@ cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, d
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return std::max(1, per_sm * sms);
   }();
-  // enough threads for the largest round (blocks + vector pairs), at most one wave; the
-  // items-per-thread target trades grid-barrier cost against per-round work (tunable with
-  // BCHDAV_JACOBI_ITEMS)
+  // a round's items (upper-triangle blocks + vector pairs) over at most one block per SM: the
+  // barrier costs the same for any grid, the float64 work shrinks with every SM added; an
+  // items-per-thread floor (BCHDAV_JACOBI_ITEMS, default 1) keeps small problems on fewer SMs
   static const int items_per_thread = []() {
     const char* env = getenv("BCHDAV_JACOBI_ITEMS");
-    return env ? std::max(1, atoi(env)) : 2;
+    return env ? std::max(1, atoi(env)) : 1;
   }();
-  long long work_items = (long long)(np / 2) * (np / 2) + (long long)np * (np / 2);
+  static const int sms = []() {
+    int dev = 0, v = kSMs;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : kSMs;
+  }();
+  const long long work_items =
+      (long long)(np / 2) * (np / 2 + 1) / 2 + (long long)np * (np / 2);
   int grid = ceil_div(work_items, (long long)kJacThreads * items_per_thread);
   if (grid > max_blocks) grid = max_blocks;
-  if (grid > 4 * kSMs) grid = 4 * kSMs;
+  if (grid > sms) grid = sms;
   if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
   JacLayout L = jac_layout(work, n);
+  cudaError_t e0 = cudaMemsetAsync(L.status, 0, 6 * sizeof(int), st);   // status, bar, where
+  if (e0 != cudaSuccess) return e0;
   int nn = n, lh = ldh, ly = ldy;
   double* wk = work;
   void* args[] = {&nn, (void*)&H, &lh, &wk, &D, &Y, &ly};

@@ -715,6 +715,10 @@ bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t l
   int st = 0;
   HCUDA(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HCUDA(cudaStreamSynchronize(h->stream));
+  if (st == 2) {
+    h->set_error(BCHDAV_ERR_TIMEOUT, "eigh: a grid barrier of the eigensolver gave up waiting");
+    return BCHDAV_ERR_TIMEOUT;
+  }
   if (st != 0) {
     h->set_error(BCHDAV_ERR_NONFINITE, "eigh: the iteration did not converge");
     return BCHDAV_ERR_NONFINITE;
@@ -1003,6 +1007,10 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     ++n_spmm;
     HCUDA(cudaStreamSynchronize(st));
     collect();
+    if (reinterpret_cast<int*>(hp + act_max)[0] == 2) {
+      h->set_error(BCHDAV_ERR_TIMEOUT, "a grid barrier of the Rayleigh-Ritz eigensolver gave up");
+      return BCHDAV_ERR_TIMEOUT;
+    }
     if (reinterpret_cast<int*>(hp + act_max)[0] != 0) {
       h->set_error(BCHDAV_ERR_NONFINITE, "Rayleigh-Ritz eigensolver did not converge");
       return BCHDAV_ERR_NONFINITE;
