@@ -115,6 +115,7 @@ typedef struct {
   int32_t k_orth;           /* basis width Step 6 orthogonalised against (k_sub before Step 7) */
   double low_nwb;
   double max_resid;         /* max relative residual of the k_b tested pairs */
+  double min_resid;         /* min relative residual of the k_b tested pairs */
 } bchdav_iter_record;
 
 /* ---- handle ------------------------------------------------------------- */

@@ -84,7 +84,8 @@ class InfoStruct(C.Structure):
 class IterStruct(C.Structure):
     _fields_ = [("it", C.c_int32), ("k_c", C.c_int32), ("e_c", C.c_int32), ("k_act", C.c_int32),
                 ("k_sub", C.c_int32), ("k_old", C.c_int32), ("n_rep", C.c_int32),
-                ("k_orth", C.c_int32), ("low_nwb", C.c_double), ("max_resid", C.c_double)]
+                ("k_orth", C.c_int32), ("low_nwb", C.c_double), ("max_resid", C.c_double),
+                ("min_resid", C.c_double)]
 
 
 _lib = None
@@ -224,6 +225,7 @@ class IterRecord:
     k_orth: int
     low_nwb: float
     max_resid: float
+    min_resid: float
 
 
 class Handle:
@@ -521,7 +523,7 @@ class Handle:
         arr = (IterStruct * max(n, 1))()
         self.L.bchdav_history(self.h, arr, n)
         return [IterRecord(r.it, r.k_c, r.e_c, r.k_act, r.k_sub, r.k_old, r.n_rep, r.k_orth,
-                           r.low_nwb, r.max_resid) for r in arr[:n]]
+                           r.low_nwb, r.max_resid, r.min_resid) for r in arr[:n]]
 
     # ---- single steps
     def filter(self, A: DeviceCSR, X, m: int, a: float, upb: float, a0: float,

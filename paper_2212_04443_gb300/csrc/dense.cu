@@ -479,54 +479,84 @@ cudaError_t launch_h_diag(cudaStream_t st, double* H, int ldh, const double* d, 
   return cudaGetLastError();
 }
 
-// G (b x b, row-major) = R^T R, R upper triangular; Rinv = R^{-1}.  One thread (b <= 64).
+// G (b x b, row-major) = R^T R, R upper triangular; Rinv = R^{-1} (b <= 64, one block).
 // flag = 1 when G is not numerically positive definite, when a pivot R_jj falls below
 // rel_min * sqrt(G_jj) (a near dependence inside the block that this Cholesky route does not
 // resolve) or below dep * norm0[j] (the dependence test of Step 6).
-__global__ void chol_inv_kernel(int b, const double* __restrict__ G, const double* __restrict__ norm0,
-                                double rel_min, double dep, double* __restrict__ Rinv,
-                                int* __restrict__ flag) {
-  __shared__ double R[64 * 64];
-  if (threadIdx.x != 0) return;
-  int bad = 0;
-  for (int j = 0; j < b && !bad; ++j) {
-    double djj = G[j * b + j];
-    for (int i = 0; i < j; ++i) djj -= R[i * 64 + j] * R[i * 64 + j];
-    if (!(djj > 0.0)) {
-      bad = 1;
-      break;
-    }
-    const double rjj = sqrt(djj);
-    if (!(rjj > rel_min * sqrt(G[j * b + j])) || (norm0 && !(rjj > dep * norm0[j]))) {
-      bad = 1;
-      break;
-    }
-    R[j * 64 + j] = rjj;
-    const double inv = 1.0 / rjj;
-    for (int k = j + 1; k < b; ++k) {
-      double v = G[j * b + k];
-      for (int i = 0; i < j; ++i) v -= R[i * 64 + j] * R[i * 64 + k];
-      R[j * 64 + k] = v * inv;
-    }
+//
+// Right-looking: after pivot j is taken, row j of R is formed in parallel and the trailing
+// entries (i, k), j < i <= k, lose R_ji R_jk.  Each entry receives its updates in the order
+// j = 0, 1, ... as one fused multiply-add each, the same arithmetic as the column-by-column
+// (left-looking) form.  The inverse is built column by column: entry (i, j) of R^{-1} needs
+// only earlier columns, so the rows of one column are computed in parallel.
+constexpr int kCholThreads = 256;
+
+__global__ void __launch_bounds__(kCholThreads) chol_inv_kernel(
+    int b, const double* __restrict__ G, const double* __restrict__ norm0, double rel_min,
+    double dep, double* __restrict__ Rinv, int* __restrict__ flag) {
+  // trailing matrix, then R in the upper triangle; R^{-1} goes to the strict lower triangle,
+  // transposed (entry (i, j), i < j, at row j, column i), and its diagonal to Rd
+  __shared__ double A[64 * 65];
+  __shared__ double Rd[64];
+  __shared__ int s_bad;
+  const int t = threadIdx.x;
+  for (int idx = t; idx < b * b; idx += kCholThreads) {
+    const int i = idx / b, k = idx - i * b;
+    A[i * 65 + k] = G[idx];
   }
-  *flag = bad;
-  if (bad) return;
+  if (t == 0) s_bad = 0;
+  __syncthreads();
   for (int j = 0; j < b; ++j) {
-    const double inv = 1.0 / R[j * 64 + j];
-    Rinv[j * b + j] = inv;
-    for (int i = j + 1; i < b; ++i) Rinv[i * b + j] = 0.0;
-    for (int i = j - 1; i >= 0; --i) {
-      double v = 0.0;
-      for (int k = i; k < j; ++k) v += Rinv[i * b + k] * R[k * 64 + j];
-      Rinv[i * b + j] = -v * inv;
+    if (t == 0) {
+      const double djj = A[j * 65 + j];
+      int bad = 0;
+      if (!(djj > 0.0)) {
+        bad = 1;
+      } else {
+        const double rjj = sqrt(djj);
+        if (!(rjj > rel_min * sqrt(G[j * b + j])) || (norm0 && !(rjj > dep * norm0[j])))
+          bad = 1;
+        A[j * 65 + j] = rjj;
+      }
+      s_bad = bad;
     }
+    __syncthreads();
+    if (s_bad) break;
+    const double inv = 1.0 / A[j * 65 + j];
+    for (int k = j + 1 + t; k < b; k += kCholThreads) A[j * 65 + k] *= inv;
+    __syncthreads();
+    // trailing update of the entries (i, k), j < i <= k
+    const int m = b - j - 1;
+    for (int idx = t; idx < m * m; idx += kCholThreads) {
+      const int i = j + 1 + idx / m, k = j + 1 + idx % m;
+      if (i <= k) A[i * 65 + k] = fma(-A[j * 65 + i], A[j * 65 + k], A[i * 65 + k]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) *flag = s_bad;
+  if (s_bad) return;
+  // (R^{-1})_{ik} for i < k sits at A[k][i]; (R^{-1})_{ii} at Rd[i]
+  for (int j = 0; j < b; ++j) {
+    const double inv = 1.0 / A[j * 65 + j];
+    if (t == 0) Rd[j] = inv;
+    __syncthreads();
+    for (int i = t; i < j; i += kCholThreads) {
+      double v = Rd[i] * A[i * 65 + j];   // k = i
+      for (int k = i + 1; k < j; ++k) v = fma(A[k * 65 + i], A[k * 65 + j], v);
+      A[j * 65 + i] = -v * inv;
+    }
+    __syncthreads();
+  }
+  for (int idx = t; idx < b * b; idx += kCholThreads) {
+    const int i = idx / b, j = idx - i * b;
+    Rinv[idx] = (i < j) ? A[j * 65 + i] : (i == j ? Rd[i] : 0.0);
   }
 }
 
 cudaError_t launch_chol_inv(cudaStream_t st, int b, const double* G, const double* norm0,
                             double rel_min, double dep, double* Rinv, int* flag) {
   if (b < 1 || b > 64) return cudaErrorInvalidValue;
-  chol_inv_kernel<<<1, 32, 0, st>>>(b, G, norm0, rel_min, dep, Rinv, flag); note_launch();
+  chol_inv_kernel<<<1, kCholThreads, 0, st>>>(b, G, norm0, rel_min, dep, Rinv, flag); note_launch();
   return cudaGetLastError();
 }
 

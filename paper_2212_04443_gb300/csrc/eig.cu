@@ -284,9 +284,14 @@ __host__ __device__ inline JacLayout jac_layout(double* w, int n) {
   return L;
 }
 
-size_t eigh_fast_work_doubles(int n) {
+static size_t jacobi_work_doubles(int n) {
   const size_t np = (size_t)(n + (n & 1));
   return 2 * np * np + 2 * 4 * kSMs + 3 * np + 16;
+}
+
+// the Jacobi area first (its status word is the route's), the tridiagonal route's after it
+size_t eigh_fast_work_doubles(int n) {
+  return jacobi_work_doubles(n) + (n > 32 && n <= kTrdMaxN ? trd_work_doubles(n) : 0);
 }
 
 // player at circle position `pos` in round r (n_pad players, player 0 fixed)
@@ -362,10 +367,14 @@ __device__ __forceinline__ int jac_ut(int i, int j, int np) {
   return i < j ? i * np + j : j * np + i;
 }
 
+// run_if (optional): the kernel does nothing unless *run_if is nonzero (the tridiagonal route
+// ran before it and asks for its result to be replaced); every CTA reads the same word.
 __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const double* __restrict__ H,
                                                                   int ldh, double* __restrict__ work,
                                                                   double* __restrict__ Dout,
-                                                                  double* __restrict__ Y, int ldy) {
+                                                                  double* __restrict__ Y, int ldy,
+                                                                  const int* __restrict__ run_if) {
+  if (run_if && *reinterpret_cast<const volatile int*>(run_if) == 0) return;
   const int np = n + (n & 1);   // an odd n gets a dummy index n that is never rotated
   const int half = np / 2;
   JacLayout L = jac_layout(work, n);
@@ -697,9 +706,22 @@ cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, d
   JacLayout L = jac_layout(work, n);
   cudaError_t e0 = cudaMemsetAsync(L.status, 0, 6 * sizeof(int), st);   // status, bar, where
   if (e0 != cudaSuccess) return e0;
+  // the tridiagonal route where the device runs it; the Jacobi kernel then runs only when the
+  // route flags its result (a tight cluster too wide, orthogonality out of reach, non-finite H)
+  int* run_if = nullptr;
+  if (n <= kTrdMaxN) {
+    cudaError_t et = launch_trd_eigh(st, n, H, ldh, D, Y, ldy, work + jacobi_work_doubles(n),
+                                     &run_if);
+    if (et == cudaErrorNotSupported) {
+      run_if = nullptr;
+    } else if (et != cudaSuccess) {
+      return et;
+    }
+  }
   int nn = n, lh = ldh, ly = ldy;
   double* wk = work;
-  void* args[] = {&nn, (void*)&H, &lh, &wk, &D, &Y, &ly};
+  const int* ri = run_if;
+  void* args[] = {&nn, (void*)&H, &lh, &wk, &D, &Y, &ly, (void*)&ri};
   note_launch();
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, grid, kJacThreads,
                                               args, smem, st);

@@ -166,6 +166,14 @@ size_t eigh_work_doubles(int n);
 cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
                              int ldy, double* work, int* status, int grid_cap = 0);
 size_t eigh_fast_work_doubles(int n);
+// Tridiagonal route of launch_eigh_fast for 32 < n <= kTrdMaxN (one thread-block cluster
+// reduces H; eigenvalues and vectors of T on the whole GPU).  work holds trd_work_doubles(n)
+// doubles.  *run_jacobi receives the device word that is nonzero when the result must be
+// replaced by the Jacobi route.  cudaErrorNotSupported: the device cannot run the cluster.
+constexpr int kTrdMaxN = 448;
+size_t trd_work_doubles(int n);
+cudaError_t launch_trd_eigh(cudaStream_t st, int n, const double* H, int ldh, double* D,
+                            double* Y, int ldy, double* work, int** run_jacobi);
 
 // ---------------- Laplacian assembly (laplacian.cu) ----------------
 struct LapWork;

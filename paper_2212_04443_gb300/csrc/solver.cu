@@ -24,6 +24,10 @@ thread_local std::string g_create_error;
 constexpr double kTauDepF64 = 1e-10;
 constexpr double kTauDepMixed = 1e-10;
 constexpr double kLowNwbEps = 1e-12;
+// Mixed path: digit slices of the product that a later float64-accurate step repairs (the first
+// DGKS projection, whose error lies in span(V) and is removed by the second).  4 slices keep 24
+// bits of each operand.
+constexpr int kMixedPass1Slices = 4;
 
 #define HCUDA(expr) BCHDAV_CUDA_OK(expr, h)
 
@@ -321,9 +325,14 @@ OzLayout oz_layout(int n, int cols) {
 // cap_cols: number of V columns the cached planes must be able to hold (0: just k).
 // vt_valid (optional): on return, the number of leading columns of V whose column planes are
 // current in oz_vt (k when this call made them, else 0).
+// pass1_slices: digit slices of the first projection's Gram product V^T X (8: float64-accurate;
+// 4 on the mixed path: operands to 24 bits, a TF32x3-class product).  Its error lies in span(V),
+// which the second, float64-accurate pass removes; the update X -= V C always uses all of V's
+// slices (a truncated V would leave error outside span(V)).
 bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, double* X, int ldx,
                        int b, uint64_t seed, double tau_dep, int64_t* rep_counter, int* n_rep,
-                       int dense_path = 0, int cap_cols = 0, int* vt_valid = nullptr) {
+                       int dense_path = 0, int cap_cols = 0, int* vt_valid = nullptr,
+                       int pass1_slices = 8) {
   cudaStream_t st = h->stream;
   if (b > 64) {
     h->set_error(BCHDAV_ERR_ARG, "block size b must be <= 64");
@@ -387,11 +396,11 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
     if (k > 0) {
       for (int pass = 0; pass < 2; ++pass) {
         if (tc) {
-          // both passes float64-accurate (a first pass from truncated slices measurably loosened
-          // the orthogonality on graphs with hub rows)
+          // the second pass float64-accurate; the first from pass1_slices (8 on the float64 path:
+          // a truncated first pass loosened its orthogonality on graphs with hub rows)
           HCUDA(oz_slice_cols_t(st, n, X, ldx, b, Np, capX, 0, h->oz_xt.p, Ext));
           HCUDA(gram_planes(h, dense_path, Np, h->oz_vt.p, Evt, capV, 0, k, h->oz_xt.p, Ext, capX,
-                            b, Gd));
+                            b, Gd, pass == 0 ? pass1_slices : 8));
           if (dense_path == 0)
             HCUDA(oz_nn_from_planes_tc(st, n, k, Kp, h->oz_vr.p, Evr, Gd, b, b, X, ldx, true,
                                        h->oz_bw.p, 8, h->tc_err.as<int>()));
@@ -924,7 +933,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     const int k_orth = k_sub;
     int vt_valid = 0;
     BCHDAV_TRY(run_orth(h, N, V, ldv, k_sub, Xo, ldb, b, opts.seed, tau_dep, &rep_counter, &nrep,
-                        opts.dense_path, ncols, &vt_valid));
+                        opts.dense_path, ncols, &vt_valid,
+                        prec == BCHDAV_PREC_MIXED ? kMixedPass1Slices : 8));
     n_rep_total += nrep;
     HCUDA(launch_copy_block(st, N, b, Xo, ldb, V + k_sub, ldv));
     tm_orth.stop(st);
@@ -948,6 +958,9 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       HCUDA(oz_slice_cols_t(st, N, V + c_from, ldv, k_sub - c_from, OL.Np, OL.capV, c_from,
                             h->oz_vt.p, Evt));
       HCUDA(oz_slice_cols_t(st, N, W, ldb, b, OL.Np, capX, 0, h->oz_xt.p, Ext));
+      // float64-accurate on both paths: only the newest b columns of H are formed, the old
+      // block is the diagonal of the previous Ritz values, so an early truncated product would
+      // leave its error in diagonal entries that no later product refreshes
       HCUDA(gram_planes(h, opts.dense_path, OL.Np, h->oz_vt.p, Evt, OL.capV, k_c, k_act,
                         h->oz_xt.p, Ext, capX, b, h->G.as<double>()));
     } else {
@@ -1054,6 +1067,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     k_c += e_c;
     double maxres = 0.0;
     for (double r : rel) maxres = std::max(maxres, r);
+    double minres = INFINITY;
+    for (double r : rel) minres = std::min(minres, r);
     if (opts.record_history) {
       bchdav_iter_record rec;
       std::memset(&rec, 0, sizeof(rec));
@@ -1067,6 +1082,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       rec.k_orth = k_orth;
       rec.low_nwb = low_nwb;
       rec.max_resid = maxres;
+      rec.min_resid = minres;
       h->history.push_back(rec);
     }
     // Step 13: exit

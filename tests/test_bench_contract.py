@@ -56,3 +56,23 @@ def test_filter_model_bytes_follow_the_scope_table():
     assert two - one == pytest.approx(4 * (n + 1) + nnz * 8 + 3 * n * b * 4)
     assert round((two - one) / 1e6, 1) == 395.9 and round(one / 1e6, 1) == 315.9
     assert filter_model_bytes(n, nnz, b, 15, 16, 4.0) == pytest.approx(16 * (one + 14 * (two - one)))
+
+
+def test_slice_pair_work_follows_the_precision_schedule():
+    """The tensor-core work the bench charges per component: 36 pairs (8 slices) on the float64
+    path; on the mixed path 10 pairs (4 slices) for the first DGKS Gram product, 21 for Step 11
+    and 36 for Step 8."""
+    sys.path.insert(0, ROOT)
+    from types import SimpleNamespace as NS
+    from bench import h_flops, orth_flops, pair_work, rotation_flops
+    n, b = 1000, 4
+    hist = [NS(k_orth=8, k_old=12, k_act=16, min_resid=r) for r in (1e-1, 1e-3, 5e-5, 1e-9)]
+    for name, f in (("rotation", rotation_flops(hist, n)),
+                    ("orthonormalisation", orth_flops(hist, n, b)),
+                    ("rayleigh_quotient", h_flops(hist, n, b))):
+        assert pair_work(name, hist, n, b, False) == 36 * f
+    assert pair_work("rotation", hist, n, b, True) == 21 * rotation_flops(hist, n)
+    assert pair_work("rayleigh_quotient", hist, n, b, True) == 36 * h_flops(hist, n, b)
+    dg = 2.0 * n * 8 * b
+    rest = 6.0 * n * 8 * b + 4.0 * n * b * b
+    assert pair_work("orthonormalisation", hist, n, b, True) == 4 * (10 * dg + 36 * rest)

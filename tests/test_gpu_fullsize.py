@@ -3,8 +3,9 @@
 * The 1,000,000-node SBM that bench.py times (100 clusters, k = 100, b = 20, m = 15,
   act_max = 300): the library-built CSR bit for bit against the oracle's; the float64 path's
   eigenvalues within 1e-10 of the oracle's (tests/golden/oracle_sbm1m.json, same iteration
-  count and k_c trajectory); the mixed path's eigenvalue error against the same golden, every
-  residual recomputed by scipy, orthonormality and lambda_1 = 0 with eigenvector D^{1/2} 1.
+  count and k_c trajectory); the mixed path's eigenvalue error against the same golden (reported,
+  and bounded by the residual tolerance: 4 tol^2 / gap per eigenvalue), every residual
+  recomputed by scipy, orthonormality and lambda_1 = 0 with eigenvector D^{1/2} 1.
 * The kNN-GMM workload reduced to 200,000 points (50 mixture components, 10-NN; k = 50,
   b = 10, m = 13, act_max = 150) and R-MAT at scale 18 (k = 64, b = 16, m = 15,
   act_max = 192), both with zero eigenvalues of multiplicity (= connected components) above
@@ -120,10 +121,20 @@ def test_sbm1m_mixed_properties_and_error(H, sbm1m):
     u = np.sqrt(L.degree.astype(float))
     u /= np.linalg.norm(u)
     assert abs(abs(u @ V[:, 0]) - 1.0) < 1e-10
-    err = np.abs(ev - np.asarray(gold["evals"])).max()
+    gev = np.asarray(gold["evals"])
+    dev = np.abs(ev - gev)
+    err = dev.max()
     print(f"sbm1m mixed path: max |lambda - lambda_oracle| = {err:.3e}, iters {info.iters} "
           f"(oracle {gold['iters']}), k_c {[h.k_c for h in hist]}")
-    assert err <= 1e-10
+    # The mixed path follows another trajectory (float32 filter, truncated products), so its
+    # converged vectors differ from the oracle's within the residual tolerance.  A Ritz value
+    # with residual r is within r^2 / gap of its eigenvalue (gap: distance to the rest of the
+    # spectrum), so the two runs' eigenvalues may differ by up to 2 tol^2 / gap: 3.2e-10 at
+    # this spectrum's smallest gap, 6.2e-7.  Gaps from the oracle's eigenvalues (the last one's
+    # left gap only), with a factor 2 for the gap estimate.
+    gaps = np.minimum(np.r_[np.inf, np.diff(gev)], np.r_[np.diff(gev), np.inf])
+    bound = 4 * tol ** 2 / gaps + 1e-12
+    assert np.all(dev <= bound), (dev / bound).max()
 
 
 def _degenerate_case(H, name, precision, orth_tol=None, exact_set=True):
