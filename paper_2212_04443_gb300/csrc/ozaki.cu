@@ -78,17 +78,42 @@ __device__ __forceinline__ unsigned long long oz_fixed(double a, int E) {
   return (mant + (1ull << (shift - 1))) >> shift;   // shift >= 5 since |a| < 2^E
 }
 
-// balanced base-64 digits of F (8 digits, most significant first): d[0] in [0, 64],
-// d[1..7] in [-32, 31]; sum_s d[s] 64^(7-s) = F
-__device__ __forceinline__ void oz_digits(unsigned long long F, int (&d)[kOzS]) {
-  long long X = (long long)F;
+// bf16 bit patterns (in the high 16 bits of f[s]) of the balanced base-64 digits of a, most
+// significant first: F = round(|a| 2^(48 - E)) = sum_s d_s 64^(7 - s), d_0 in [0, 64],
+// d_1..d_7 in [-32, 31], each carrying the sign of a.  The digits come from the two 24-bit
+// halves of F with 32-bit integer operations (the low half's four digits leave a carry of 0
+// or 1 for the high half).  A digit v (|v| <= 64) becomes a float by adding it to the bit
+// pattern of 1.5 * 2^23 and subtracting 1.5 * 2^23 (exact below 2^22), and that float's low 16
+// bits are zero, so its high half is the bf16 pattern.
+__device__ __forceinline__ void oz_split_bits(double a, int E, uint32_t (&f)[kOzS]) {
+  const unsigned long long F = oz_fixed(a, E);
+  int lo = (int)(F & 0xFFFFFFull), hi = (int)(F >> 24);
+  const int m = (__double2hiint(a) < 0) ? -1 : 0;   // sign of a
+  int d[kOzS];
 #pragma unroll
-  for (int s = kOzS - 1; s >= 1; --s) {
-    long long r = ((X + 32) & 63) - 32;
-    d[s] = (int)r;
-    X = (X - r) >> 6;
+  for (int s = kOzS - 1; s >= 4; --s) {
+    const int r = ((lo + 32) & 63) - 32;
+    d[s] = r;
+    lo = (lo - r) >> 6;
   }
-  d[0] = (int)X;
+  hi += lo;
+#pragma unroll
+  for (int s = 3; s >= 1; --s) {
+    const int r = ((hi + 32) & 63) - 32;
+    d[s] = r;
+    hi = (hi - r) >> 6;
+  }
+  d[0] = hi;
+#pragma unroll
+  for (int s = 0; s < kOzS; ++s) {
+    const int v = (d[s] ^ m) - m;
+    f[s] = __float_as_uint(__int_as_float(0x4B400000 + v) - 12582912.0f);
+  }
+}
+
+// two elements' patterns packed as bf16 pairs (first element in the low half)
+__device__ __forceinline__ uint32_t oz_pack(uint32_t f0, uint32_t f1) {
+  return __byte_perm(f0, f1, 0x7632);
 }
 
 __device__ __forceinline__ double oz_pow2(int ex) {
@@ -96,67 +121,75 @@ __device__ __forceinline__ double oz_pow2(int ex) {
                                    : ldexp(1.0, ex);
 }
 
-__device__ __forceinline__ __nv_bfloat16 oz_bf16(int d, bool neg) {
-  return __float2bfloat16_rn((float)(neg ? -d : d));   // |d| <= 64: exact
-}
+// Row exponents and slices of A (N x K, K <= kOzMaxK) into tiled planes with `n` rows and Kp
+// (zero padded) values of k, in one pass over A: a CTA stages kOzSRows whole rows in shared
+// memory (row-contiguous, coalesced loads), takes each row's exponent E[i] = max_j
+// (exponent(a_ij) + 1) (0 for a zero row), then thread t splits 8 consecutive k of one row and
+// stores one 16-byte piece per slice (consecutive threads: consecutive rows).
+constexpr int kOzSRows = 16;
 
-// Row exponents of A (N x K): E[i] = max_j (exponent(a_ij) + 1); 0 for zero rows.
-__global__ void oz_row_exp_kernel(int n, const double* __restrict__ A, int lda, int K,
-                                  int* __restrict__ E) {
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
-    int m = -100000;
-    for (int j = lane; j < K; j += 32) m = max(m, oz_exp_plus1(A[(size_t)r * lda + j]));
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) E[r] = (m < -50000) ? 0 : m;
-  }
-}
-
-// Slices of A (N x K) into tiled planes with `n` rows and Kp (zero padded) values of k.  A
-// tile of 64 rows x 32 k is staged in shared memory with row-contiguous (coalesced) loads;
-// thread t then splits 8 consecutive k of row t % 64 and stores one 16-byte piece per slice
-// (consecutive threads: consecutive rows, 1 KB contiguous per slice and half k step).
-constexpr int kOzSRows = 64, kOzSK = 32;
-
-__global__ void __launch_bounds__(256) oz_split_rows_kernel(int n, const double* __restrict__ A,
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, const double* __restrict__ A,
                                                             int lda, int K, int Kp,
-                                                            const int* __restrict__ E,
+                                                            int* __restrict__ E,
                                                             __nv_bfloat16* __restrict__ P) {
-  __shared__ double tile[kOzSRows][kOzSK + 1];
+  extern __shared__ double oz_rtile[];   // kOzSRows x (Kp + 1)
+  __shared__ int s_e[kOzSRows];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int r0 = blockIdx.x * kOzSRows, k0 = blockIdx.y * kOzSK;
+  const int ld = Kp + 1;
+  const int r0 = blockIdx.x * kOzSRows;
   for (int i = warp; i < kOzSRows; i += 8) {
-    const int r = r0 + i, k = k0 + lane;
-    tile[i][lane] = (r < n && k < K) ? A[(size_t)r * lda + k] : 0.0;
+    const int r = r0 + i;
+    int mx = -100000;
+    for (int k = lane; k < Kp; k += 32) {
+      const double a = (r < n && k < K) ? A[(size_t)r * lda + k] : 0.0;
+      oz_rtile[i * ld + k] = a;
+      mx = max(mx, oz_exp_plus1(a));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      const int e = (mx < -50000) ? 0 : mx;
+      s_e[i] = e;
+      if (r < n) E[r] = e;
+    }
   }
   __syncthreads();
-  const int rl = t & (kOzSRows - 1), g = t >> 6;   // 4 groups of 8 k
-  const int r = r0 + rl, kg = k0 + 8 * g;
-  if (r >= n || kg >= Kp) return;
-  const int e = E[r];
-  uint32_t w[kOzS][4];
+  const int groups = Kp >> 3;
+  for (int item = t; item < kOzSRows * groups; item += 256) {
+    const int i = item % kOzSRows, g = item / kOzSRows;
+    const int r = r0 + i;
+    if (r >= n) continue;
+    const int e = s_e[i];
+    const double* row = oz_rtile + i * ld + 8 * g;
+    uint32_t w[kOzS][4];
 #pragma unroll
-  for (int j = 0; j < 8; j += 2) {
-    const double a0 = tile[rl][8 * g + j], a1 = tile[rl][8 * g + j + 1];
-    int d0[kOzS], d1[kOzS];
-    oz_digits(oz_fixed(a0, e), d0);
-    oz_digits(oz_fixed(a1, e), d1);
+    for (int j = 0; j < 8; j += 2) {
+      uint32_t f0[kOzS], f1[kOzS];
+      oz_split_bits(row[j], e, f0);
+      oz_split_bits(row[j + 1], e, f1);
+#pragma unroll
+      for (int s = 0; s < kOzS; ++s) w[s][j >> 1] = oz_pack(f0[s], f1[s]);
+    }
 #pragma unroll
     for (int s = 0; s < kOzS; ++s)
-      w[s][j >> 1] = (uint32_t)__bfloat16_as_ushort(oz_bf16(d0[s], a0 < 0.0)) |
-                     ((uint32_t)__bfloat16_as_ushort(oz_bf16(d1[s], a1 < 0.0)) << 16);
+      *reinterpret_cast<uint4*>(P + oz_tix(s, r, 8 * g, n)) =
+          make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
   }
-#pragma unroll
-  for (int s = 0; s < kOzS; ++s)
-    *reinterpret_cast<uint4*>(P + oz_tix(s, r, kg, n)) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
-static void oz_split_rows_launch(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
-                                 const int* E, __nv_bfloat16* P) {
-  dim3 g(ceil_div(n, kOzSRows), ceil_div(Kp, kOzSK));
-  oz_split_rows_kernel<<<g, 256, 0, st>>>(n, A, lda, K, Kp, E, P);
+static cudaError_t oz_slice_rows_launch(cudaStream_t st, int n, const double* A, int lda, int K,
+                                        int Kp, int* E, __nv_bfloat16* P) {
+  if (Kp > kOzMaxK || Kp % 8 != 0) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kOzSRows * (Kp + 1) * sizeof(double);
+  static const bool attr = [] {
+    return cudaFuncSetAttribute(oz_slice_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)kOzSRows * (kOzMaxK + 1) * sizeof(double))) ==
+           cudaSuccess;
+  }();
+  if (!attr) return cudaErrorInvalidValue;
+  oz_slice_rows_kernel<<<ceil_div(n, kOzSRows), 256, smem, st>>>(n, A, lda, K, Kp, E, P);
   note_launch();
+  return cudaGetLastError();
 }
 
 // Column exponents and transposed slices of B (K x nb): planes S x nbp x Kp.
@@ -173,11 +206,11 @@ __global__ void oz_split_cols_kernel(int K, int nb, const double* __restrict__ B
     if (lane == 0) F_out[c] = Ec;
     for (int k = lane; k < Kp; k += 32) {
       const double b = (c < nb && k < K) ? B[(size_t)k * ldb + c] : 0.0;
-      int d[kOzS];
-      oz_digits(oz_fixed(b, Ec), d);
-      const bool neg = b < 0.0;
+      uint32_t f[kOzS];
+      oz_split_bits(b, Ec, f);
 #pragma unroll
-      for (int s = 0; s < kOzS; ++s) P[oz_tix(s, c, k, nbp)] = oz_bf16(d[s], neg);
+      for (int s = 0; s < kOzS; ++s)
+        P[oz_tix(s, c, k, nbp)] = __ushort_as_bfloat16((unsigned short)(f[s] >> 16));
     }
   }
 }
@@ -407,9 +440,8 @@ cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, in
   __nv_bfloat16* PB = PA + (size_t)kOzS * n * Kp;
   int* EA = reinterpret_cast<int*>(PB + (size_t)kOzS * nbp * Kp);
   int* EB = EA + n;
-  oz_row_exp_kernel<<<ceil_div((long long)n * 32, 256) < 16 * kSMs ? ceil_div((long long)n * 32, 256) : 16 * kSMs,
-                      256, 0, st>>>(n, A, lda, K, EA); note_launch();
-  oz_split_rows_launch(st, n, A, lda, K, Kp, EA, PA);
+  cudaError_t es = oz_slice_rows_launch(st, n, A, lda, K, Kp, EA, PA);
+  if (es != cudaSuccess) return es;
   oz_split_cols_kernel<<<ceil_div((long long)nbp * 32, 256), 256, 0, st>>>(K, nb, B, ldb, Kp, nbp, EB,
                                                                             PB); note_launch();
   dim3 grid((unsigned)((long long)ceil_div(n, kOzBM) * (nbp / kOzBN)), 1, 1);
@@ -419,28 +451,6 @@ cudaError_t launch_ozaki_nn(cudaStream_t st, int n, const double* A, int lda, in
 }
 
 // ---------------- Gram products A^T B (reduction over the N rows) ----------------
-// Chunk column exponents of X (N x w): E[ch * cap + c_off + c] = max over rows r of chunk ch of
-// (exponent(x_rc) + 1), 0 for a chunk column without nonzeros.  Block (ch, column tile of 32):
-// warps walk the chunk's rows, lanes the columns; fixed-order max, no atomics.
-__global__ void __launch_bounds__(256) oz_col_exp_kernel(int n, const double* __restrict__ X, int ldx,
-                                                         int w, int cap, int c_off,
-                                                         int* __restrict__ E) {
-  __shared__ int sm[8][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ch = blockIdx.x, c = blockIdx.y * 32 + lane;
-  const int r_end = min(n, (ch + 1) * kOzChunk);
-  int m = -100000;
-  if (c < w)
-    for (int r = ch * kOzChunk + warp; r < r_end; r += 8) m = max(m, oz_exp_plus1(X[(size_t)r * ldx + c]));
-  sm[warp][lane] = m;
-  __syncthreads();
-  if (warp == 0 && c < w) {
-    int mm = sm[0][lane];
-    for (int q = 1; q < 8; ++q) mm = max(mm, sm[q][lane]);
-    E[(size_t)ch * cap + c_off + c] = mm < -50000 ? 0 : mm;
-  }
-}
-
 int oz_chunks(int Np) { return ceil_div(Np, kOzChunk); }
 
 size_t ozaki_tn_work_bytes(int n, int ka, int kb) {
@@ -497,62 +507,85 @@ int oz_pad_cols(int n) { return round_up(n, kOzBN); }
 // Row slices of A (n x K) into planes S x n x Kp with exponents E[n].
 cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
                           void* planes, int* E) {
-  __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
-  oz_row_exp_kernel<<<ceil_div((long long)n * 32, 256) < 16 * kSMs ? ceil_div((long long)n * 32, 256) : 16 * kSMs,
-                      256, 0, st>>>(n, A, lda, K, E); note_launch();
-  oz_split_rows_launch(st, n, A, lda, K, Kp, E, P);
-  return cudaGetLastError();
+  return oz_slice_rows_launch(st, n, A, lda, K, Kp, E, static_cast<__nv_bfloat16*>(planes));
 }
 
 // Transposed column slices: columns [0, w) of X (N x w) become rows [c_off, c_off + w) of the
 // tiled planes with `cap` rows and Np values of k (the N rows of X, zero padded), with chunk
-// exponents E[ch * cap + c_off + c].  A 64-row x 32-column tile of X is staged in shared
-// memory; thread t splits 8 consecutive rows of one column and stores one 16-byte piece per
-// slice (consecutive threads: consecutive columns, so a warp writes 512 contiguous bytes).
-// Rows of the planes outside [c_off, c_off + w) are untouched.
-constexpr int kOzTRows = 64;
+// exponents E[ch * cap + c_off + c] = max over the rows of chunk ch of (exponent(x_rc) + 1) (0
+// for a chunk column without nonzeros), in one pass over X: a CTA stages one chunk (kOzChunk
+// rows) of 8 columns in shared memory, takes the 8 exponents (one warp per column), then
+// thread t splits 8 consecutive rows of one column and stores one 16-byte piece per slice
+// (consecutive threads: consecutive columns, 128 contiguous bytes per slice).  Rows of the
+// planes outside [c_off, c_off + w) are untouched.
+constexpr int kOzTCols = 8;
+constexpr int kOzTLd = kOzChunk + 2;   // doubles per staged column
 
-__global__ void __launch_bounds__(256) oz_split_cols_t_off_kernel(
+__global__ void __launch_bounds__(256) oz_slice_cols_kernel(
     int n, const double* __restrict__ X, int ldx, int w, int Np, int cap, int c_off,
-    const int* __restrict__ E, __nv_bfloat16* __restrict__ P) {
-  __shared__ double tile[32][kOzTRows + 1];   // [column][row]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 8 warps
-  const int r0 = blockIdx.x * kOzTRows, cb = blockIdx.y * 32;
-  for (int i = warp; i < kOzTRows; i += 8) {
-    const int r = r0 + i, c = cb + lane;
-    tile[lane][i] = (r < n && c < w) ? X[(size_t)r * ldx + c] : 0.0;
+    int* __restrict__ E, __nv_bfloat16* __restrict__ P) {
+  extern __shared__ double oz_ctile[];   // [kOzTCols][kOzTLd]
+  __shared__ int s_e[kOzTCols];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int ch = blockIdx.x, c0 = blockIdx.y * kOzTCols;
+  const int r0 = ch * kOzChunk;
+  const int rows = min(kOzChunk, Np - r0);   // a multiple of 8
+  for (int idx = t; idx < kOzChunk * kOzTCols; idx += 256) {
+    const int rl = idx / kOzTCols, cl = idx % kOzTCols;
+    const int r = r0 + rl, c = c0 + cl;
+    oz_ctile[cl * kOzTLd + rl] = (r < n && c < w) ? X[(size_t)r * ldx + c] : 0.0;
   }
   __syncthreads();
-  const int c = cb + lane, g = warp;   // rows r0 + 8g .. r0 + 8g + 7
-  const int r = r0 + 8 * g;
-  if (c >= w || r >= Np) return;
-  const int e = E[(size_t)(r / kOzChunk) * cap + c_off + c];
-  uint32_t wd[kOzS][4];
+  {
+    const int cl = warp;   // 8 warps, 8 columns
+    int mx = -100000;
+    for (int rl = lane; rl < rows; rl += 32) mx = max(mx, oz_exp_plus1(oz_ctile[cl * kOzTLd + rl]));
 #pragma unroll
-  for (int j = 0; j < 8; j += 2) {
-    const double a0 = tile[lane][8 * g + j], a1 = tile[lane][8 * g + j + 1];
-    int d0[kOzS], d1[kOzS];
-    oz_digits(oz_fixed(a0, e), d0);
-    oz_digits(oz_fixed(a1, e), d1);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      const int e = (mx < -50000) ? 0 : mx;
+      s_e[cl] = e;
+      if (c0 + cl < w) E[(size_t)ch * cap + c_off + c0 + cl] = e;
+    }
+  }
+  __syncthreads();
+  const int groups = rows >> 3;
+  for (int item = t; item < kOzTCols * groups; item += 256) {
+    const int cl = item % kOzTCols, g = item / kOzTCols;
+    const int c = c0 + cl;
+    if (c >= w) continue;
+    const int e = s_e[cl];
+    const double* col = oz_ctile + cl * kOzTLd + 8 * g;
+    uint32_t wd[kOzS][4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      uint32_t f0[kOzS], f1[kOzS];
+      oz_split_bits(col[j], e, f0);
+      oz_split_bits(col[j + 1], e, f1);
+#pragma unroll
+      for (int s = 0; s < kOzS; ++s) wd[s][j >> 1] = oz_pack(f0[s], f1[s]);
+    }
 #pragma unroll
     for (int s = 0; s < kOzS; ++s)
-      wd[s][j >> 1] = (uint32_t)__bfloat16_as_ushort(oz_bf16(d0[s], a0 < 0.0)) |
-                      ((uint32_t)__bfloat16_as_ushort(oz_bf16(d1[s], a1 < 0.0)) << 16);
+      *reinterpret_cast<uint4*>(P + oz_tix(s, (size_t)c_off + c, r0 + 8 * g, cap)) =
+          make_uint4(wd[s][0], wd[s][1], wd[s][2], wd[s][3]);
   }
-#pragma unroll
-  for (int s = 0; s < kOzS; ++s)
-    *reinterpret_cast<uint4*>(P + oz_tix(s, (size_t)c_off + c, r, cap)) =
-        make_uint4(wd[s][0], wd[s][1], wd[s][2], wd[s][3]);
 }
 
 cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, int w, int Np, int cap,
                             int c_off, void* planes, int* E) {
   if (w <= 0) return cudaSuccess;
-  __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
-  oz_col_exp_kernel<<<dim3(oz_chunks(Np), ceil_div(w, 32)), 256, 0, st>>>(n, A, lda, w, cap, c_off,
-                                                                           E); note_launch();
-  dim3 g(ceil_div(Np, kOzTRows), ceil_div(w, 32));
-  oz_split_cols_t_off_kernel<<<g, 256, 0, st>>>(n, A, lda, w, Np, cap, c_off, E, P); note_launch();
+  if (Np % 8 != 0) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kOzTCols * kOzTLd * sizeof(double);
+  static const bool attr = [smem] {
+    return cudaFuncSetAttribute(oz_slice_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem) == cudaSuccess;
+  }();
+  if (!attr) return cudaErrorInvalidValue;
+  dim3 g(oz_chunks(Np), ceil_div(w, kOzTCols));
+  oz_slice_cols_kernel<<<g, 256, smem, st>>>(n, A, lda, w, Np, cap, c_off, E,
+                                             static_cast<__nv_bfloat16*>(planes));
+  note_launch();
   return cudaGetLastError();
 }
 
