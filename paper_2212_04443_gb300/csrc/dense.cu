@@ -493,16 +493,31 @@ constexpr int kCholThreads = 256;
 
 __global__ void __launch_bounds__(kCholThreads) chol_inv_kernel(
     int b, const double* __restrict__ G, const double* __restrict__ norm0, double rel_min,
-    double dep, double* __restrict__ Rinv, int* __restrict__ flag) {
+    double dep, double* __restrict__ Rinv, int* __restrict__ flag, double* __restrict__ colscale) {
   // trailing matrix, then R in the upper triangle; R^{-1} goes to the strict lower triangle,
   // transposed (entry (i, j), i < j, at row j, column i), and its diagonal to Rd
   __shared__ double A[64 * 65];
   __shared__ double Rd[64];
+  __shared__ double Ds[64];   // equilibration D_jj (1 without colscale)
   __shared__ int s_bad;
   const int t = threadIdx.x;
+  for (int j = t; j < b; j += kCholThreads) {
+    double dj = 1.0;
+    if (colscale != nullptr) {
+      // 2^-e with 2^(e-1) <= sqrt(G_jj) < 2^e, so that the scaled diagonal lies in [1/4, 1)
+      const double gjj = G[j * b + j];
+      if (gjj > 0.0 && gjj < INFINITY) {
+        const int e = (int)((__double_as_longlong(sqrt(gjj)) >> 52) & 0x7FF) - 1022;
+        dj = (e > -1021 && e < 1022) ? __longlong_as_double((long long)(1023 - e) << 52) : 1.0;
+      }
+      colscale[j] = dj;
+    }
+    Ds[j] = dj;
+  }
+  __syncthreads();
   for (int idx = t; idx < b * b; idx += kCholThreads) {
     const int i = idx / b, k = idx - i * b;
-    A[i * 65 + k] = G[idx];
+    A[i * 65 + k] = G[idx] * Ds[i] * Ds[k];   // exact: powers of two
   }
   if (t == 0) s_bad = 0;
   __syncthreads();
@@ -514,7 +529,8 @@ __global__ void __launch_bounds__(kCholThreads) chol_inv_kernel(
         bad = 1;
       } else {
         const double rjj = sqrt(djj);
-        if (!(rjj > rel_min * sqrt(G[j * b + j])) || (norm0 && !(rjj > dep * norm0[j])))
+        if (!(rjj > rel_min * sqrt(G[j * b + j]) * Ds[j]) ||
+            (norm0 && !(rjj > dep * norm0[j] * Ds[j])))
           bad = 1;
         A[j * 65 + j] = rjj;
       }
@@ -554,9 +570,10 @@ __global__ void __launch_bounds__(kCholThreads) chol_inv_kernel(
 }
 
 cudaError_t launch_chol_inv(cudaStream_t st, int b, const double* G, const double* norm0,
-                            double rel_min, double dep, double* Rinv, int* flag) {
+                            double rel_min, double dep, double* Rinv, int* flag,
+                            double* colscale) {
   if (b < 1 || b > 64) return cudaErrorInvalidValue;
-  chol_inv_kernel<<<1, kCholThreads, 0, st>>>(b, G, norm0, rel_min, dep, Rinv, flag); note_launch();
+  chol_inv_kernel<<<1, kCholThreads, 0, st>>>(b, G, norm0, rel_min, dep, Rinv, flag, colscale); note_launch();
   return cudaGetLastError();
 }
 

@@ -93,8 +93,12 @@ cudaError_t launch_h_update(cudaStream_t st, double* H, int ldh, const double* G
 // H = diag(d[0:k]) (ldh x ldh cleared up to k).
 cudaError_t launch_h_diag(cudaStream_t st, double* H, int ldh, const double* d, int k, int clear);
 // Cholesky G = R^T R of a small Gram matrix and R^{-1} (see dense.cu for the flag rules).
+// With colscale (b doubles, output): G is first equilibrated by exact powers of two,
+// G' = D G D with D_jj = colscale[j] ~ 1 / sqrt(G_jj), and R^{-1} is that of G' (so that
+// (X D) R'^{-1} = X R^{-1}).
 cudaError_t launch_chol_inv(cudaStream_t st, int b, const double* G, const double* norm0,
-                            double rel_min, double dep, double* Rinv, int* flag);
+                            double rel_min, double dep, double* Rinv, int* flag,
+                            double* colscale = nullptr);
 // Non-finite check: flag |= any(!isfinite(x)).
 cudaError_t launch_check_finite(cudaStream_t st, int n, int w, const double* X, int ldx, int* flag);
 
@@ -120,8 +124,9 @@ size_t oz_planes_bytes(size_t rows, size_t kp);
 int oz_pad_k(int k);      // k padded to the k step (16)
 int oz_pad_rows(int m);   // rows padded to the row tile (64)
 int oz_pad_cols(int n);   // columns padded to the column tile (32)
+// colscale (optional, K doubles, exact powers of two): slices of A diag(colscale).
 cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
-                          void* planes, int* E);
+                          void* planes, int* E, const double* colscale = nullptr);
 cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, int w, int Np, int cap,
                             int c_off, void* planes, int* E);
 cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const int* EA, int capA,

@@ -130,6 +130,7 @@ constexpr int kOzSRows = 16;
 
 __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, const double* __restrict__ A,
                                                             int lda, int K, int Kp,
+                                                            const double* __restrict__ colscale,
                                                             int* __restrict__ E,
                                                             __nv_bfloat16* __restrict__ P) {
   extern __shared__ double oz_rtile[];   // kOzSRows x (Kp + 1)
@@ -141,7 +142,8 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, const double*
     const int r = r0 + i;
     int mx = -100000;
     for (int k = lane; k < Kp; k += 32) {
-      const double a = (r < n && k < K) ? A[(size_t)r * lda + k] : 0.0;
+      double a = (r < n && k < K) ? A[(size_t)r * lda + k] : 0.0;
+      if (colscale != nullptr && k < K) a *= colscale[k];   // a power of two: exact
       oz_rtile[i * ld + k] = a;
       mx = max(mx, oz_exp_plus1(a));
     }
@@ -178,7 +180,8 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, const double*
 }
 
 static cudaError_t oz_slice_rows_launch(cudaStream_t st, int n, const double* A, int lda, int K,
-                                        int Kp, int* E, __nv_bfloat16* P) {
+                                        int Kp, int* E, __nv_bfloat16* P,
+                                        const double* colscale = nullptr) {
   if (Kp > kOzMaxK || Kp % 8 != 0) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kOzSRows * (Kp + 1) * sizeof(double);
   static const bool attr = [] {
@@ -187,7 +190,7 @@ static cudaError_t oz_slice_rows_launch(cudaStream_t st, int n, const double* A,
            cudaSuccess;
   }();
   if (!attr) return cudaErrorInvalidValue;
-  oz_slice_rows_kernel<<<ceil_div(n, kOzSRows), 256, smem, st>>>(n, A, lda, K, Kp, E, P);
+  oz_slice_rows_kernel<<<ceil_div(n, kOzSRows), 256, smem, st>>>(n, A, lda, K, Kp, colscale, E, P);
   note_launch();
   return cudaGetLastError();
 }
@@ -506,8 +509,9 @@ int oz_pad_cols(int n) { return round_up(n, kOzBN); }
 
 // Row slices of A (n x K) into planes S x n x Kp with exponents E[n].
 cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
-                          void* planes, int* E) {
-  return oz_slice_rows_launch(st, n, A, lda, K, Kp, E, static_cast<__nv_bfloat16*>(planes));
+                          void* planes, int* E, const double* colscale) {
+  return oz_slice_rows_launch(st, n, A, lda, K, Kp, E, static_cast<__nv_bfloat16*>(planes),
+                              colscale);
 }
 
 // Transposed column slices: columns [0, w) of X (N x w) become rows [c_off, c_off + w) of the

@@ -307,6 +307,8 @@ cudaError_t gram_planes(bchdav_handle h, int dense_path, int Np, const void* PA,
 // Where the cached slices of V live: column planes of V (S x capV x Np, exponents after them) in
 // oz_vt and row planes (S x n x KpCap, exponents after them) in oz_vr.  Both are sized for the
 // largest subspace `cols` once, so that the exponent arrays stay at fixed offsets for every call.
+// KpCap is at least 64: the row planes' buffer also takes the block's own row planes (b <= 64
+// columns) for the CholQR step of Step 6.
 struct OzLayout {
   int Np, capV, KpCap;
   size_t vt_planes, vr_planes;
@@ -316,7 +318,7 @@ OzLayout oz_layout(int n, int cols) {
   cols = std::max(cols, 1);
   L.Np = oz_pad_k(n);
   L.capV = oz_pad_rows(cols);
-  L.KpCap = oz_pad_k(cols);
+  L.KpCap = oz_pad_k(std::max(cols, 64));
   L.vt_planes = oz_planes_bytes(L.capV, L.Np);
   L.vr_planes = oz_planes_bytes(n, L.KpCap);
   return L;
@@ -343,7 +345,7 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   const size_t part_doubles = (size_t)chunks * std::max(ka_max, b) * b;
   BCHDAV_TRY(h->ensure(h->part, part_doubles * sizeof(double)));
   const size_t g_words = (size_t)std::max(ka_max * b, 64 * 64);
-  BCHDAV_TRY(h->ensure(h->G, (g_words + 64 * 64 + 16) * sizeof(double)));
+  BCHDAV_TRY(h->ensure(h->G, (g_words + 64 * 64 + 8 + 64 + 16) * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->norm0, (size_t)(3 * 64 + 16) * sizeof(double)));
   BCHDAV_TRY(h->ensure(h->small, inblock_gs_scratch_doubles(b) * sizeof(double) + 64));
   BCHDAV_TRY(h->ensure_aux(256));
@@ -392,8 +394,13 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
     }
   }
   double* Gd = h->G.as<double>();
+  bool vr_reused = false;   // the V row planes' buffer holds X's row planes (tensor-core CholQR)
   for (int attempt = 0; attempt < b + 16; ++attempt) {
     if (k > 0) {
+      if (tc && vr_reused) {
+        HCUDA(oz_slice_rows(st, n, V, ldv, k, Kp, h->oz_vr.p, Evr));
+        vr_reused = false;
+      }
       for (int pass = 0; pass < 2; ++pass) {
         if (tc) {
           // the second pass float64-accurate; the first from pass1_slices (8 on the float64 path:
@@ -425,18 +432,37 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
       HCUDA(cudaMemcpyAsync(norm0_d, hp, b * sizeof(double), cudaMemcpyHostToDevice, st));
       bool ok = true;
       for (int pass = 0; pass < 2 && ok; ++pass) {
-        // the b x b Gram matrix and X R^{-1} are small (2 N b^2 flops): plain float64
-        HCUDA(launch_gemm_tn_partial(st, n, X, ldx, b, X, ldx, b, h->part.as<double>(), chunks));
-        HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, b * b, Gd, 1.0));
+        // G = X^T X and X <- X R^{-1}: float64-accurate slice products on the tensor cores
+        // (path 0; X's row planes go to the V row planes' buffer, free once both projections
+        // are done), plain float64 otherwise
+        if (dense_path == 0) {
+          HCUDA(oz_slice_cols_t(st, n, X, ldx, b, Np, capX, 0, h->oz_xt.p, Ext));
+          HCUDA(gram_planes(h, dense_path, Np, h->oz_xt.p, Ext, capX, 0, b, h->oz_xt.p, Ext, capX,
+                            b, Gd));
+        } else {
+          HCUDA(launch_gemm_tn_partial(st, n, X, ldx, b, X, ldx, b, h->part.as<double>(), chunks));
+          HCUDA(launch_reduce_partials(st, h->part.as<double>(), chunks, b * b, Gd, 1.0));
+        }
+        // the tensor-core product X R^{-1} slices the rows of X, each to one exponent: its
+        // columns are first brought to comparable norms (exact powers of two, D), and
+        // X R^{-1} = (X D) R'^{-1} with R' the Cholesky factor of D G D
+        double* dscale = dense_path == 0 ? Gd + g_words + 64 * 64 + 8 : nullptr;
         HCUDA(launch_chol_inv(st, b, Gd, pass == 0 ? norm0_d : nullptr, pass == 0 ? 1e-4 : 0.5,
-                              tau_dep, Rinv, flag));
+                              tau_dep, Rinv, flag, dscale));
         HCUDA(cudaMemcpyAsync(hp + 64, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
         HCUDA(cudaStreamSynchronize(st));
         if (reinterpret_cast<int*>(hp + 64)[0] != 0) {
           ok = false;
           break;
         }
-        HCUDA(launch_gemm_tri_inplace(st, n, X, ldx, b, Rinv, b));
+        if (dense_path == 0) {
+          HCUDA(oz_slice_rows(st, n, X, ldx, b, oz_pad_k(b), h->oz_vr.p, Evr, dscale));
+          vr_reused = true;
+          HCUDA(oz_nn_from_planes_tc(st, n, b, oz_pad_k(b), h->oz_vr.p, Evr, Rinv, b, b, X, ldx,
+                                     false, h->oz_bw.p, 8, h->tc_err.as<int>()));
+        } else {
+          HCUDA(launch_gemm_tri_inplace(st, n, X, ldx, b, Rinv, b));
+        }
       }
       if (ok) return BCHDAV_OK;
       // a failed first pass left X untouched; a failed second pass (never expected after a

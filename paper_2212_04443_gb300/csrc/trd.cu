@@ -13,7 +13,7 @@
 //     after one.  Q = P_0 P_1 ... P_{n-3} is then accumulated backwards with Q held by columns
 //     (column c in CTA c mod kTrdCl): w^T = v^T Q and Q <- Q - tau v w^T need no exchange, only
 //     v, read from the owners of the rows.  T splits where |e_i| <= eps ||T||.
-//  2. trd_bisect_kernel, eight lanes per eigenvalue: multisection (8 points per round) on Sturm
+//  2. trd_bisect_kernel, one warp per eigenvalue: multisection (64 points per round) on Sturm
 //     counts (signs of the leading minors of T - x I) of the eigenvalue's block of T.
 //  3. trd_vectors_kernel, one warp per eigenvalue: inverse iteration (two solves with T - lambda
 //     I, LU with partial pivoting) from a pseudo-random start.  Eigenvalues closer than
@@ -115,13 +115,14 @@ struct TrdSmem {
   double* pv;     // [kTrdCl] partial p^T v
   double* red;    // [64]
   double* rowv;   // [32] one value per own row (p_r v_r, or a squared entry)
-  double* sc;     // [8] scalars of the current column: tau, scale, beta, K
+  double* sraw;   // [32] A x for own rows, x the column before scaling
+  double* sc;     // [8] scalars of the current column: tau, scale, beta, K, 1 - scale alpha
 };
 
 __host__ __device__ inline size_t trd_smem_doubles(int n) {
   const int ldA = n | 1;
   return (size_t)kTrdMaxRows * ldA + (size_t)kTrdMaxRows * n + 2 * (size_t)n + 2 * (size_t)n +
-         2 * (size_t)n + (size_t)n + 2 * (size_t)kTrdCl + 64 + 32 + 8;
+         2 * (size_t)n + (size_t)n + 2 * (size_t)kTrdCl + 64 + 32 + 32 + 8;
 }
 
 __device__ inline TrdSmem trd_smem(double* base, int n) {
@@ -138,7 +139,8 @@ __device__ inline TrdSmem trd_smem(double* base, int n) {
   S.pv = S.sq + kTrdCl;
   S.red = S.pv + kTrdCl;
   S.rowv = S.red + 64;
-  S.sc = S.rowv + 32;
+  S.sraw = S.rowv + 32;
+  S.sc = S.sraw + 32;
   return S;
 }
 
@@ -147,6 +149,46 @@ __device__ inline TrdSmem trd_smem(double* base, int n) {
 __device__ __forceinline__ void trd_push(cg::cluster_group& cl, double* local, int off, double val) {
 #pragma unroll 4
   for (int c = 0; c < kTrdCl; ++c) cl.map_shared_rank(local, c)[off] = val;
+}
+
+// Dot products of R rows (or columns) of a warp with one vector, two accumulators per row,
+// reduced together across the lanes: R independent dependent chains instead of one.
+template <int R>
+__device__ __forceinline__ void trd_dots(const double* const (&row)[4], const double* __restrict__ x,
+                                         int m, int lane, double (&out)[4]) {
+  double acc[R][2];
+#pragma unroll
+  for (int u = 0; u < R; ++u) acc[u][0] = acc[u][1] = 0.0;
+  for (int q = lane; q < m; q += 64) {
+    const double x0 = x[q];
+    const bool two = q + 32 < m;
+    const double x1 = two ? x[q + 32] : 0.0;
+    const int q1 = two ? q + 32 : q;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      acc[u][0] = fma(row[u][q], x0, acc[u][0]);
+      acc[u][1] = fma(row[u][q1], x1, acc[u][1]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) out[u] = acc[u][0] + acc[u][1];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) out[u] += __shfl_xor_sync(0xffffffffu, out[u], o);
+  }
+}
+
+__device__ __forceinline__ void trd_dots_n(int cnt, const double* const (&row)[4],
+                                           const double* __restrict__ x, int m, int lane,
+                                           double (&out)[4]) {
+  switch (cnt) {   // warp-uniform
+    case 4: trd_dots<4>(row, x, m, lane, out); break;
+    case 3: trd_dots<3>(row, x, m, lane, out); break;
+    case 2: trd_dots<2>(row, x, m, lane, out); break;
+    case 1: trd_dots<1>(row, x, m, lane, out); break;
+    default: break;
+  }
 }
 
 __global__ void __launch_bounds__(kTrdThreads, 1)
@@ -184,15 +226,19 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
   cl.sync();
   double tn = 0.0;   // running max of |d_i| + |e_{i-1}| + |e_i| (CTA 0, thread 32)
   double e_prev = 0.0;
-  // Scalar work (square roots, divisions, sums over the CTAs or the own rows) is done by one
-  // warp and handed to the others through shared memory: GB300's float64 pipe is narrow, and
-  // the same operation repeated by every warp would cost as much as a row of the matrix.
+  // GB300's float64 pipe is narrow and its results come late, so a column's critical path is a
+  // count of dependent float64 operations.  Scalar work (square root, divisions, sums over the
+  // CTAs or the own rows) is done by one warp and handed to the others through shared memory;
+  // the matrix-vector product starts from the unscaled column x at once, beside that warp:
+  // A v = scale A x + (1 - scale alpha) A e_0, as v = scale x except v_0 = 1.  Dot products keep
+  // two accumulators per row and a warp's rows (at most four) are reduced together.
+  constexpr int kRowsW = (kTrdMaxRows + 6) / 7;   // own rows per warp 1..7
   for (int i = 0; i < n - 2; ++i) {
     const int m = n - i - 1;   // trailing size: rows / columns i+1 .. n-1
     double* x = S.xb + (i & 1) * n;
     const int lr0 = (i + 1 - me + kTrdCl - 1) / kTrdCl;   // first own row > i
-    // reflector from the pushed column x = A(i+1:n-1, i)
     if (warp == 0) {
+      // reflector from the pushed column x = A(i+1:n-1, i)
       const double sig = warp_sum(lane < kTrdCl ? S.sq[lane] : 0.0);
       if (lane == 0) {
         const double alpha = x[0];
@@ -205,29 +251,34 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
         S.sc[0] = tau;
         S.sc[1] = scale;
         S.sc[2] = beta;
+        S.sc[4] = (sig != 0.0) ? fma(-scale, alpha, 1.0) : 1.0;
         S.taus[i] = tau;
       }
+    } else {
+      // raw products A(r, i+1:n-1) x for the own rows lr0 + (warp - 1) + 7 u
+      const int first = lr0 + warp - 1;
+      const int cnt = first < nown ? min(kRowsW, (nown - first + 6) / 7) : 0;
+      const double* Ar[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) Ar[u] = S.A + (u < cnt ? first + 7 * u : 0) * ldA + i + 1;
+      double sum[4];
+      trd_dots_n(cnt, Ar, x, m, lane, sum);
+      if (lane == 0)
+        for (int u = 0; u < cnt; ++u) S.sraw[first + 7 * u] = sum[u];
     }
     __syncthreads();
-    const double tau = S.sc[0];
-    {
-      const double scale = S.sc[1];
-      for (int q = t; q < m; q += kTrdThreads) x[q] = (q == 0) ? 1.0 : x[q] * scale;
-    }
-    __syncthreads();
-    // v into the own rows' column i (kept for the accumulation of Q); p = tau A v on own rows
-    for (int lr = lr0 + warp; lr < nown; lr += kTrdThreads / 32) {
-      const int r = me + kTrdCl * lr;
-      const double* Ar = S.A + lr * ldA + i + 1;
-      double s = 0.0;
-      for (int q = lane; q < m; q += 32) s = fma(Ar[q], x[q], s);
-      s = warp_sum(s);
-      const double p = tau * s;
-      if (lane == 0) {
-        S.A[lr * ldA + i] = x[r - i - 1];
-        S.rowv[lr] = p * x[r - i - 1];
+    const double tau = S.sc[0], scale = S.sc[1], c0 = S.sc[4];
+    // p = tau A v on own rows (one thread per row and destination CTA); v into column i
+    for (int idx = t; idx < (nown - lr0) * kTrdCl; idx += kTrdThreads) {
+      const int lr = lr0 + idx / kTrdCl, dst = idx % kTrdCl;
+      const int r = me + kTrdCl * lr, qr = r - i - 1;
+      const double p = tau * fma(scale, S.sraw[lr], c0 * S.A[lr * ldA + i + 1]);
+      cl.map_shared_rank(S.pf, dst)[qr] = p;
+      if (dst == 0) {
+        const double vr = (qr == 0) ? 1.0 : x[qr] * scale;
+        S.A[lr * ldA + i] = vr;
+        S.rowv[lr] = p * vr;
       }
-      if (lane < kTrdCl) cl.map_shared_rank(S.pf, lane)[r - i - 1] = p;
     }
     if (me == 0 && t == 32) {
       const double di = cl.map_shared_rank(S.A, i % kTrdCl)[(i / kTrdCl) * ldA + i];
@@ -237,7 +288,8 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
       tn = fmax(tn, fabs(di) + fabs(e_prev) + fabs(beta));
       e_prev = beta;
     }
-    __syncthreads();
+    __syncthreads();   // A(:, i) holds v before x is scaled in place
+    for (int q = t; q < m; q += kTrdThreads) x[q] = (q == 0) ? 1.0 : x[q] * scale;
     if (warp == 0) {
       const double pvp = warp_sum((lr0 + lane < nown) ? S.rowv[lr0 + lane] : 0.0);
       if (lane < kTrdCl) cl.map_shared_rank(S.pv, lane)[me] = pvp;
@@ -273,7 +325,8 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
       const int r = me + kTrdCl * lr, qr = r - i - 1;
       const double vr = x[qr], wr = S.w[qr];
       double* a = S.A + lr * ldA + i + 1;
-      for (int q = 1 + lane; q < m; q += 32) a[q] = a[q] - vr * S.w[q] - wr * x[q];
+#pragma unroll 4
+      for (int q = 1 + lane; q < m; q += 32) a[q] = fma(-wr, x[q], fma(-vr, S.w[q], a[q]));
     }
     cl.sync();
   }
@@ -343,14 +396,22 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
     const double* v = S.vq + (i & 1) * n;
     const int m = n - i - 1;
     const int lc0 = (i + 1 - me + kTrdCl - 1) / kTrdCl;   // first own column > i
-    for (int lc = lc0 + warp; lc < ncol; lc += kTrdThreads / 32) {
-      double* qc = S.Qc + lc * n + i + 1;   // column entries, rows i+1 .. n-1
-      double s = 0.0;
-      for (int q = lane; q < m; q += 32) s = fma(v[q], qc[q], s);
+    // a warp's own columns (at most four) at once
+    const int first = lc0 + warp;
+    const int cnt = first < ncol ? min(4, (ncol - first + 7) / 8) : 0;
+    const double* qr[4];
+    double* qc[4];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      const double f = tau * s;
-      for (int q = lane; q < m; q += 32) qc[q] = fma(-f, v[q], qc[q]);
+    for (int u = 0; u < 4; ++u) {
+      qc[u] = S.Qc + (u < cnt ? first + 8 * u : 0) * n + i + 1;   // rows i+1 .. n-1
+      qr[u] = qc[u];
+    }
+    double f[4];
+    trd_dots_n(cnt, qr, v, m, lane, f);
+    for (int u = 0; u < cnt; ++u) {
+      const double fu = tau * f[u];
+#pragma unroll 4
+      for (int q = lane; q < m; q += 32) qc[u][q] = fma(-fu, v[q], qc[u][q]);
     }
   }
   __syncthreads();
@@ -361,94 +422,114 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
   cl.sync();   // no CTA leaves while others may still read its shared memory
 }
 
-// Number of eigenvalues of the block [s0, s1) of T / ||T|| below x: the sign changes of its
-// leading principal minors P_0 = 1, P_i = (d_i - x) P_{i-1} - e_{i-1}^2 P_{i-2} (the Sturm
-// sequence; a P_i that is exactly zero takes the sign opposite to P_{i-1}, as a pivot of the
-// LDL^T factorisation of T - x I that is taken negative).  Three float64 operations per entry
-// and no division; |P_i / P_{i-1}| <= 3 on the scaled matrix, so a rescaling by a power of two
-// every eight entries keeps the minors in range.
-__device__ __forceinline__ int trd_sturm(const double* __restrict__ dn, const double* __restrict__ e2n,
-                                         int s0, int s1, double x) {
-  double pm = 1.0;           // P_{i-2}
-  double pc = dn[s0] - x;    // P_{i-1}
-  if (pc == 0.0) pc = -0x1p-600;
-  int cnt = pc < 0.0;
+// Number of eigenvalues of the block [s0, s1) of T / ||T|| below x0 and below x1: the sign
+// changes of the leading principal minors P_0 = 1, P_i = (d_i - x) P_{i-1} - e_{i-1}^2 P_{i-2}
+// (the Sturm sequence).  A P_i that is exactly zero takes the sign opposite to P_{i-1} (as a
+// pivot of the LDL^T factorisation of T - x I that is taken negative), magnitude |P_{i-1}|
+// 2^-600, set with integer operations so that the dependent chain from one minor to the next
+// is a single float64 FMA; the two shifts' chains are interleaved.  |P_i / P_{i-1}| <= 3 on
+// the scaled matrix, so a rescaling by a power of two every eight entries keeps them in range.
+__device__ __forceinline__ double trd_nonzero(double pn, double pc) {
+  const int hi = __double2hiint(pn), lo = __double2loint(pn);
+  const int hp = __double2hiint(pc);
+  const int ex = (hp >> 20) & 0x7ff;
+  const double alt = __hiloint2double((~hp & (int)0x80000000) | ((ex > 601 ? ex - 600 : 1) << 20), 0);
+  return (((hi & 0x7fffffff) | lo) == 0) ? alt : pn;
+}
+
+__device__ __forceinline__ void trd_rescale(double& pc, double& pm) {
+  const int ex = ((__double2hiint(pc) >> 20) & 0x7ff) - 1023;
+  if (ex > 300 || ex < -300) {
+    const double f = __hiloint2double((1023 - ex) << 20, 0);   // 2^-ex
+    pc *= f;
+    pm *= f;
+  }
+}
+
+__device__ __forceinline__ void trd_sturm2(const double* __restrict__ dn,
+                                           const double* __restrict__ e2n, int s0, int s1,
+                                           double x0, double x1, int& c0, int& c1) {
+  double pm0 = 1.0, pm1 = 1.0;
+  double pc0 = trd_nonzero(dn[s0] - x0, pm0), pc1 = trd_nonzero(dn[s0] - x1, pm1);
+  c0 = pc0 < 0.0;
+  c1 = pc1 < 0.0;
   for (int i = s0 + 1; i < s1; ++i) {
-    double pn = fma(dn[i] - x, pc, -e2n[i - 1] * pm);
-    if (pn == 0.0) pn = copysign(fabs(pc) * 0x1p-600, -pc);   // (+-0 after underflow: same sign)
-    cnt += (__double2hiint(pn) ^ __double2hiint(pc)) < 0;
-    pm = pc;
-    pc = pn;
+    const double di = dn[i], ei = e2n[i - 1];
+    double pn0 = fma(di - x0, pc0, -ei * pm0);
+    double pn1 = fma(di - x1, pc1, -ei * pm1);
+    pn0 = trd_nonzero(pn0, pc0);
+    pn1 = trd_nonzero(pn1, pc1);
+    c0 += (__double2hiint(pn0) ^ __double2hiint(pc0)) < 0;
+    c1 += (__double2hiint(pn1) ^ __double2hiint(pc1)) < 0;
+    pm0 = pc0;
+    pc0 = pn0;
+    pm1 = pc1;
+    pc1 = pn1;
     if (((i - s0) & 7) == 0) {
-      const int ex = ((__double2hiint(pc) >> 20) & 0x7ff) - 1023;
-      if (ex > 300 || ex < -300) {
-        const double f = __hiloint2double((1023 - ex) << 20, 0);   // 2^-ex
-        pc *= f;
-        pm *= f;
-      }
+      trd_rescale(pc0, pm0);
+      trd_rescale(pc1, pm1);
     }
   }
-  return cnt;
 }
 
 // one warp per eigenvalue in the vector kernel, two warps per CTA (the float64 pipes of all SMs)
 constexpr int kTrdEigWarps = 2;
-// Multisection: kBisLanes lanes per eigenvalue place kBisLanes points in its interval each round
-// (log2(kBisLanes + 1) bits per round).  Fewer points per round cost more rounds but less
-// float64 work in all: 8 points give 17 rounds of 8 Sturm counts, 32 points 11 rounds of 32.
-constexpr int kBisLanes = 8;
-constexpr int kBisGroups = 32 / kBisLanes;   // eigenvalues per warp
 
+// Multisection, one warp per eigenvalue (one warp per CTA): each lane counts at two points, so
+// a round places 64 points in the interval (6 bits per round, 9 rounds for float64).  The
+// rounds are bound by the latency of the Sturm chain, not by float64 throughput.
 __global__ void __launch_bounds__(32) trd_bisect_kernel(int n, TrdLayout L) {
-  const int lane = threadIdx.x & 31, g = lane / kBisLanes, l = lane % kBisLanes;
-  const int j = blockIdx.x * kBisGroups + g;
-  const bool live = j < n;
-  const int jj = live ? j : n - 1;
-  const int s0 = L.bstart[jj], s1 = L.bend[jj], k = jj - s0;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x;
+  if (j >= n) return;
+  const int s0 = L.bstart[j], s1 = L.bend[j], k = j - s0;
+  if (s1 - s0 == 1) {
+    if (lane == 0) L.lam[j] = L.d[s0];
+    return;
+  }
   const double tn = L.ctl->tnorm;
   const double* dn = L.dn;
   const double* e2n = L.e2n;
   // Gershgorin interval of the block, on the scaled matrix
   double lo = INFINITY, hi = -INFINITY;
-  for (int i = s0 + l; i < s1; i += kBisLanes) {
+  for (int i = s0 + lane; i < s1; i += 32) {
     const double el = (i > s0) ? sqrt(e2n[i - 1]) : 0.0;
     const double er = (i < s1 - 1) ? sqrt(e2n[i]) : 0.0;
     lo = fmin(lo, dn[i] - el - er);
     hi = fmax(hi, dn[i] + el + er);
   }
 #pragma unroll
-  for (int o = kBisLanes / 2; o > 0; o >>= 1) {
+  for (int o = 16; o > 0; o >>= 1) {
     lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
   lo -= 4.0 * kTrdEps;
   hi += 4.0 * kTrdEps;
   const double atol = 0.5 * kTrdEps;   // of ||T||
-  bool done = !live || s1 - s0 == 1;
-  for (int round = 0; round < 96; ++round) {
+  for (int round = 0; round < 64; ++round) {
     const double width = hi - lo;
-    if (!(width > fmax(2.0 * kTrdEps * fmax(fabs(lo), fabs(hi)), atol))) done = true;
-    if (__all_sync(0xffffffffu, done)) break;
-    const double xl = lo + width * ((double)(l + 1) / (double)(kBisLanes + 1));
-    const int cnt = done ? 0 : trd_sturm(dn, e2n, s0, s1, xl);
-    // points of this group whose count exceeds k: the eigenvalue lies below them
-    const unsigned above =
-        (__ballot_sync(0xffffffffu, cnt > k) >> (g * kBisLanes)) & ((1u << kBisLanes) - 1);
-    const int first = above ? __ffs(above) - 1 : kBisLanes;
-    const double xf = __shfl_sync(0xffffffffu, xl, first % kBisLanes, kBisLanes);
-    const double xp = __shfl_sync(0xffffffffu, xl, (first + kBisLanes - 1) % kBisLanes, kBisLanes);
-    const double nlo = (first == 0) ? lo : xp;
-    const double nhi = (first == kBisLanes) ? hi : xf;
-    if (!done) {
-      if (!(nhi - nlo < width)) {
-        done = true;   // no progress (rounding)
-      } else {
-        lo = nlo;
-        hi = nhi;
-      }
-    }
+    if (!(width > fmax(2.0 * kTrdEps * fmax(fabs(lo), fabs(hi)), atol))) break;
+    // points p = 2 lane + c, c = 0, 1, at lo + width (p + 1) / 65
+    const double x0 = lo + width * ((double)(2 * lane + 1) * (1.0 / 65.0));
+    const double x1 = lo + width * ((double)(2 * lane + 2) * (1.0 / 65.0));
+    int c0, c1;
+    trd_sturm2(dn, e2n, s0, s1, x0, x1, c0, c1);
+    const unsigned a0 = __ballot_sync(0xffffffffu, c0 > k), a1 = __ballot_sync(0xffffffffu, c1 > k);
+    // first point whose count exceeds k: the eigenvalue lies below it, above the one before
+    const int f0 = a0 ? 2 * (__ffs(a0) - 1) : 64, f1 = a1 ? 2 * (__ffs(a1) - 1) + 1 : 64;
+    const int first = min(f0, f1);
+    const double xf0 = __shfl_sync(0xffffffffu, x0, (first >> 1) & 31);
+    const double xf1 = __shfl_sync(0xffffffffu, x1, (first >> 1) & 31);
+    const int prev = first - 1;
+    const double xp0 = __shfl_sync(0xffffffffu, x0, (prev >> 1) & 31);
+    const double xp1 = __shfl_sync(0xffffffffu, x1, (prev >> 1) & 31);
+    const double nhi = (first == 64) ? hi : ((first & 1) ? xf1 : xf0);
+    const double nlo = (first == 0) ? lo : ((prev & 1) ? xp1 : xp0);
+    if (!(nhi - nlo < width)) break;   // no progress (rounding)
+    lo = nlo;
+    hi = nhi;
   }
-  if (live && l == 0) L.lam[j] = (s1 - s0 == 1) ? L.d[s0] : 0.5 * (lo + hi) * tn;
+  if (lane == 0) L.lam[j] = 0.5 * (lo + hi) * tn;
 }
 
 // LU factors with partial pivoting of T_b - lambda I (block [s0, s1)): the elimination of a
@@ -722,7 +803,7 @@ cudaError_t launch_trd_eigh(cudaStream_t st, int n, const double* H, int ldh, do
   note_launch();
   cudaError_t e = cudaLaunchKernelEx(&cfg, trd_reduce_kernel, n, H, ldh, L);
   if (e != cudaSuccess) return e;
-  trd_bisect_kernel<<<ceil_div(n, kBisGroups), 32, 0, st>>>(n, L); note_launch();
+  trd_bisect_kernel<<<n, 32, 0, st>>>(n, L); note_launch();
   trd_vectors_kernel<<<ceil_div(n, kTrdEigWarps), kTrdEigWarps * 32, 0, st>>>(n, L); note_launch();
   const int tiles = ceil_div(n, 16);
   trd_gemm_kernel<0><<<dim3(tiles, tiles, 2), 256, 0, st>>>(n, L, D, Y, ldy); note_launch();
