@@ -122,23 +122,28 @@ __device__ __forceinline__ double oz_pow2(int ex) {
 }
 
 // Row exponents and slices of A (N x K, K <= kOzMaxK) into tiled planes with `n` rows and Kp
-// (zero padded) values of k, in one pass over A: a CTA stages kOzSRows whole rows in shared
-// memory (row-contiguous, coalesced loads), takes each row's exponent E[i] = max_j
-// (exponent(a_ij) + 1) (0 for a zero row), then thread t splits 8 consecutive k of one row and
-// stores one 16-byte piece per slice (consecutive threads: consecutive rows).
-constexpr int kOzSRows = 16;
+// (zero padded) values of k, in one pass over A: a CTA stages R whole rows in shared memory
+// (row-contiguous, coalesced loads; R ~ 4096 / Kp, 16 to 128), takes each row's exponent
+// E[i] = max_j (exponent(a_ij) + 1) (0 for a zero row), then thread t splits 8 consecutive k of
+// one row and stores one 16-byte piece per slice (consecutive threads: consecutive rows).
+constexpr int kOzSRowsMin = 16, kOzSRowsMax = 128;
+__host__ __device__ inline int oz_srows(int Kp) {
+  const int r = 4096 / (Kp > 0 ? Kp : 1);
+  return r < kOzSRowsMin ? kOzSRowsMin : (r > kOzSRowsMax ? kOzSRowsMax : r);
+}
 
 __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, const double* __restrict__ A,
                                                             int lda, int K, int Kp,
                                                             const double* __restrict__ colscale,
                                                             int* __restrict__ E,
                                                             __nv_bfloat16* __restrict__ P) {
-  extern __shared__ double oz_rtile[];   // kOzSRows x (Kp + 1)
-  __shared__ int s_e[kOzSRows];
+  extern __shared__ double oz_rtile[];   // R x (Kp + 1)
+  __shared__ int s_e[kOzSRowsMax];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int ld = Kp + 1;
-  const int r0 = blockIdx.x * kOzSRows;
-  for (int i = warp; i < kOzSRows; i += 8) {
+  const int R = oz_srows(Kp);
+  const int r0 = blockIdx.x * R;
+  for (int i = warp; i < R; i += 8) {
     const int r = r0 + i;
     int mx = -100000;
     for (int k = lane; k < Kp; k += 32) {
@@ -157,8 +162,8 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, const double*
   }
   __syncthreads();
   const int groups = Kp >> 3;
-  for (int item = t; item < kOzSRows * groups; item += 256) {
-    const int i = item % kOzSRows, g = item / kOzSRows;
+  for (int item = t; item < R * groups; item += 256) {
+    const int i = item % R, g = item / R;
     const int r = r0 + i;
     if (r >= n) continue;
     const int e = s_e[i];
@@ -183,14 +188,17 @@ static cudaError_t oz_slice_rows_launch(cudaStream_t st, int n, const double* A,
                                         int Kp, int* E, __nv_bfloat16* P,
                                         const double* colscale = nullptr) {
   if (Kp > kOzMaxK || Kp % 8 != 0) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)kOzSRows * (Kp + 1) * sizeof(double);
+  const int R = oz_srows(Kp);
+  const size_t smem = (size_t)R * (Kp + 1) * sizeof(double);
   static const bool attr = [] {
+    size_t mx = 0;
+    for (int kp = 16; kp <= kOzMaxK; kp += 16)
+      mx = std::max(mx, (size_t)oz_srows(kp) * (kp + 1) * sizeof(double));
     return cudaFuncSetAttribute(oz_slice_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((size_t)kOzSRows * (kOzMaxK + 1) * sizeof(double))) ==
-           cudaSuccess;
+                                (int)mx) == cudaSuccess;
   }();
   if (!attr) return cudaErrorInvalidValue;
-  oz_slice_rows_kernel<<<ceil_div(n, kOzSRows), 256, smem, st>>>(n, A, lda, K, Kp, colscale, E, P);
+  oz_slice_rows_kernel<<<ceil_div(n, R), 256, smem, st>>>(n, A, lda, K, Kp, colscale, E, P);
   note_launch();
   return cudaGetLastError();
 }
