@@ -881,8 +881,9 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
   double* hp = h->host_pinned;
   h->history.clear();
 
-  Timer tm_total, tm_filter, tm_orth, tm_spmm, tm_h, tm_eig, tm_rot, tm_res;
-  Timer* timers[] = {&tm_total, &tm_filter, &tm_orth, &tm_spmm, &tm_h, &tm_eig, &tm_rot, &tm_res};
+  Timer tm_total, tm_filter, tm_orth, tm_spmm, tm_h, tm_eig, tm_rot, tm_res, tm_res2;
+  Timer* timers[] = {&tm_total, &tm_filter, &tm_orth, &tm_spmm, &tm_h,
+                     &tm_eig,   &tm_rot,    &tm_res,  &tm_res2};
   for (Timer* t : timers) t->init();
   struct Cleanup {
     Timer** t;
@@ -1030,10 +1031,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     tm_rot.stop(st);
     // Step 12: residuals of the leading k_b Ritz pairs
     const int nt = std::min(b, k_act);
-    // the mixed path also keeps the residuals of the next k_b Ritz vectors: after locking they
-    // become filter inputs (Step 17) and are filtered in residual form; only the first nt
-    // decide convergence (Step 12)
-    const int nres = prec == BCHDAV_PREC_MIXED ? std::min(2 * b, k_act) : nt;
+    const int nres = nt;
     tm_res.start(st);
     int nparts = 0;
     HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c, ldv, nres, Dd,
@@ -1076,6 +1074,23 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     const int e_c = (int)order.size();
     for (int j = 0; j < nt; ++j)
       if (!(rel[j] <= tol)) order.push_back(j);
+    // mixed path: after a lock, Step 17's next filter inputs reach e_c Ritz vectors beyond the
+    // tested block; their float64 residuals are formed now (Ritz values still in Dd), so that
+    // every Ritz vector the filter takes is filtered in residual form
+    int n_avail = nt;
+    if (prec == BCHDAV_PREC_MIXED && e_c > 0) {
+      const int n_ext = std::min(e_c, k_act - nt);
+      if (n_ext > 0) {
+        int np2 = 0;
+        tm_res2.start(st);
+        HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c + nt, ldv, n_ext,
+                                Dd + nt, h->part.as<double>(), &np2, h->Rres.as<double>() + nt,
+                                ldr, negd, h->long_rows()));
+        tm_res2.stop(st);
+        ++n_spmm;
+        n_avail = nt + n_ext;
+      }
+    }
     bool identity = true;
     for (int j = 0; j < nt; ++j) identity = identity && (order[j] == j);
     if (!identity) {
@@ -1147,7 +1162,7 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     }
     for (int j = 0; j < n_r; ++j) {
       const int pre = e_c + j;   // position in the active block after the partition
-      if (pre < nres) {
+      if (pre < n_avail) {
         mix_src[n_i + j] = pre < nt ? order[pre] : pre;
         mix_theta[n_i + j] = Dh[pre];
       }
@@ -1219,9 +1234,9 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     info->ms_h = tm_h.acc;
     info->ms_eig = tm_eig.acc;
     info->ms_rot = tm_rot.acc;
-    info->ms_resid = tm_res.acc;
+    info->ms_resid = tm_res.acc + tm_res2.acc;
     info->ms_other = tm_total.acc - (tm_filter.acc + tm_orth.acc + tm_spmm.acc + tm_h.acc +
-                                     tm_eig.acc + tm_rot.acc + tm_res.acc);
+                                     tm_eig.acc + tm_rot.acc + tm_res.acc + tm_res2.acc);
     info->filter_bytes = filter_bytes;
     info->filter_ms_kernels = tm_filter.acc;
     info->n_kernel_launches =
@@ -1256,10 +1271,15 @@ bchdav_status bchdav_solve_host(bchdav_handle h, int32_t n, int64_t nnz, const i
   HCUDA(cudaMemcpyAsync(h->hval.p, val, (size_t)nnz * sizeof(double), cudaMemcpyHostToDevice, st));
   if (opts.k_init > 0 && opts.v_init) {
     BCHDAV_TRY(h->ensure(h->hvinit, (size_t)n * opts.k_init * sizeof(double)));
-    HCUDA(cudaMemcpy2DAsync(h->hvinit.p, (size_t)opts.k_init * sizeof(double), opts.v_init,
-                            (size_t)opts.ld_v_init * sizeof(double),
-                            (size_t)opts.k_init * sizeof(double), (size_t)n,
+    if (opts.ld_v_init == opts.k_init)   // contiguous: one linear copy (a pitched copy of
+                                         // short rows moves row by row)
+      HCUDA(cudaMemcpyAsync(h->hvinit.p, opts.v_init, (size_t)n * opts.k_init * sizeof(double),
                             cudaMemcpyHostToDevice, st));
+    else
+      HCUDA(cudaMemcpy2DAsync(h->hvinit.p, (size_t)opts.k_init * sizeof(double), opts.v_init,
+                              (size_t)opts.ld_v_init * sizeof(double),
+                              (size_t)opts.k_init * sizeof(double), (size_t)n,
+                              cudaMemcpyHostToDevice, st));
     opts.v_init = h->hvinit.as<double>();
     opts.ld_v_init = opts.k_init;
   }
