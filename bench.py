@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sbm1m")
     ap.add_argument("--workers", type=int, default=8, help="concurrent solves of a batch workload")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched leg (the first 64 graphs of the batch512 workload)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned start-block leg (a network trained on three graphs of "
                          "the workload's family, evaluated on a held-out one)")
@@ -394,6 +396,12 @@ def run_ours(args):
             out["warm_start"] = warm_start_leg(args.workload, prec, stream)
         except Exception as exc:   # report, keep the main line
             out["warm_start"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+    # ---- many small graphs in one call (the batch512 workload's first 64 graphs)
+    if not args.no_batched and rank == 0 and not args.workload.startswith("batch"):
+        try:
+            out["batched"] = batched_leg(prec, args.workers)
+        except Exception as exc:   # report, keep the main line
+            out["batched"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload, info.iters)
@@ -581,6 +589,52 @@ def warm_start_leg(workload, prec, stream):
     del As, Rs, Us, V0
     Ht.release_workspace()
     return out
+
+
+def batched_leg(prec, workers, n_graphs=64):
+    """bchdav_solve_batched on the first 64 graphs of the batch512 workload (the same seeds and
+    distribution): graphs/s of one warm call, per-graph latency percentiles, launches per graph."""
+    import torch
+    import synth
+    import paper_2212_04443_gb300 as P
+    graphs = _batch_head(n_graphs)
+    Hb = P.Handle()
+    As = [Hb.build_laplacian(g.n, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda())
+          for g in graphs]
+    cs = [int(g.labels.max()) + 1 for g in graphs]
+    ks, bs = cs, [min(c, 8) for c in cs]
+
+    def once():
+        return Hb.solve_batched(As, ks, bs, [11] * n_graphs, [0] * n_graphs, 1e-8,
+                                precision=prec, seed=0, workers=workers, itmax=200)
+
+    once()
+    torch.cuda.synchronize()
+    l0 = P.launch_count()
+    t0 = time.perf_counter()
+    _, _, infos, per = once()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    launches = P.launch_count() - l0
+    out = {"graphs": n_graphs, "sum_n": int(sum(g.n for g in graphs)),
+           "workers": workers, "graphs_per_s": round(n_graphs / t, 2), "seconds": round(t, 3),
+           "latency_ms": {"p50": round(float(np.percentile(per, 50)), 2),
+                          "p99": round(float(np.percentile(per, 99)), 2)},
+           "launches_per_graph": round(launches / n_graphs, 1),
+           "converged": all(i.status == 0 for i in infos)}
+    Hb.release_workspace()
+    return out
+
+
+def _batch_head(n_graphs):
+    """The first n_graphs graphs of synth.batch_sbm(512), generated without the rest."""
+    import math
+    import synth
+    g = synth.rng(4)
+    ns = np.floor(np.exp(g.uniform(math.log(2000), math.log(200000), 512))).astype(np.int64)
+    cs = g.integers(4, 33, 512)
+    return [synth.sbm_edges(int(ns[i]), int(cs[i]), d_in=12.0, d_out=1.5, seed=1000 + i)
+            for i in range(n_graphs)]
 
 
 def oracle_problem(w):
