@@ -124,9 +124,10 @@ size_t oz_planes_bytes(size_t rows, size_t kp);
 int oz_pad_k(int k);      // k padded to the k step (16)
 int oz_pad_rows(int m);   // rows padded to the row tile (64)
 int oz_pad_cols(int n);   // columns padded to the column tile (32)
-// colscale (optional, K doubles, exact powers of two): slices of A diag(colscale).
+// colscale (optional, K doubles, exact powers of two): slices of A diag(colscale).  slices: the
+// leading planes written (a product that reads fewer slices needs only those).
 cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
-                          void* planes, int* E, const double* colscale = nullptr);
+                          void* planes, int* E, const double* colscale = nullptr, int slices = 8);
 cudaError_t oz_slice_cols_t(cudaStream_t st, int n, const double* A, int lda, int w, int Np, int cap,
                             int c_off, void* planes, int* E);
 cudaError_t oz_gram_from_planes(cudaStream_t st, int Np, const void* PA, const int* EA, int capA,

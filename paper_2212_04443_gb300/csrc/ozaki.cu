@@ -135,7 +135,7 @@ __host__ __device__ inline int oz_srows(int Kp) {
 __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, const double* __restrict__ A,
                                                             int lda, int K, int Kp,
                                                             const double* __restrict__ colscale,
-                                                            int* __restrict__ E,
+                                                            int slices, int* __restrict__ E,
                                                             __nv_bfloat16* __restrict__ P) {
   extern __shared__ double oz_rtile[];   // R x (Kp + 1)
   __shared__ int s_e[kOzSRowsMax];
@@ -179,14 +179,15 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int n, const double*
     }
 #pragma unroll
     for (int s = 0; s < kOzS; ++s)
-      *reinterpret_cast<uint4*>(P + oz_tix(s, r, 8 * g, n)) =
-          make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+      if (s < slices)   // a product that reads only the leading slices needs only those
+        *reinterpret_cast<uint4*>(P + oz_tix(s, r, 8 * g, n)) =
+            make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
   }
 }
 
 static cudaError_t oz_slice_rows_launch(cudaStream_t st, int n, const double* A, int lda, int K,
                                         int Kp, int* E, __nv_bfloat16* P,
-                                        const double* colscale = nullptr) {
+                                        const double* colscale = nullptr, int slices = kOzS) {
   if (Kp > kOzMaxK || Kp % 8 != 0) return cudaErrorInvalidValue;
   const int R = oz_srows(Kp);
   const size_t smem = (size_t)R * (Kp + 1) * sizeof(double);
@@ -198,7 +199,8 @@ static cudaError_t oz_slice_rows_launch(cudaStream_t st, int n, const double* A,
                                 (int)mx) == cudaSuccess;
   }();
   if (!attr) return cudaErrorInvalidValue;
-  oz_slice_rows_kernel<<<ceil_div(n, R), 256, smem, st>>>(n, A, lda, K, Kp, colscale, E, P);
+  oz_slice_rows_kernel<<<ceil_div(n, R), 256, smem, st>>>(n, A, lda, K, Kp, colscale, slices, E,
+                                                          P);
   note_launch();
   return cudaGetLastError();
 }
@@ -517,9 +519,10 @@ int oz_pad_cols(int n) { return round_up(n, kOzBN); }
 
 // Row slices of A (n x K) into planes S x n x Kp with exponents E[n].
 cudaError_t oz_slice_rows(cudaStream_t st, int n, const double* A, int lda, int K, int Kp,
-                          void* planes, int* E, const double* colscale) {
+                          void* planes, int* E, const double* colscale, int slices) {
+  if (slices < 1 || slices > kOzS) return cudaErrorInvalidValue;
   return oz_slice_rows_launch(st, n, A, lda, K, Kp, E, static_cast<__nv_bfloat16*>(planes),
-                              colscale);
+                              colscale, slices);
 }
 
 // Transposed column slices: columns [0, w) of X (N x w) become rows [c_off, c_off + w) of the

@@ -1018,7 +1018,8 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       // into the same buffer, then V is overwritten in place (the planes hold all of A)
       int* Evr = reinterpret_cast<int*>(h->oz_vr.as<char>() + OL.vr_planes);
       const int Kp = oz_pad_k(k_old);
-      HCUDA(oz_slice_rows(st, N, V + k_c, ldv, k_old, Kp, h->oz_vr.p, Evr));
+      HCUDA(oz_slice_rows(st, N, V + k_c, ldv, k_old, Kp, h->oz_vr.p, Evr, nullptr,
+                          opts.dense_path == 0 ? slices_rr : 8));
       if (opts.dense_path == 0)
         HCUDA(oz_nn_from_planes_tc(st, N, k_old, Kp, h->oz_vr.p, Evr, Ym, act_max, k_act, V + k_c,
                                    ldv, false, h->oz_bw.p, slices_rr, h->tc_err.as<int>()));

@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_kernel(
         const unsigned tbase = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(buf * NS * kTcN);
 #pragma unroll
         for (int g = 0; g < kTcN / 8; ++g) {
+          if (nt * kTcN + g * 8 >= wk.ncols) break;   // no output column left in this tile
           unsigned r[NS][8];
 #pragma unroll
           for (int L = 0; L < NS; ++L) tmem_ld8(r[L], tbase + (unsigned)(L * kTcN + g * 8));
