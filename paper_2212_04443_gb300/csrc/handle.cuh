@@ -44,6 +44,7 @@ struct bchdav_handle_s {
   DevBuf km, km_x;              // clustering: centroids, sums, seeding state; transposed features
   DevBuf lz;                    // Lanczos bound estimate: three vectors, coefficients, T_k
   DevBuf vchk;                  // count of non-finite entries of a caller's V_init
+  DevBuf vallo, ddx;            // mixed path: A's values' low float parts; split block scratch
   const bchdav::SpmmLong* long_rows() const { return lg.n_seg > 0 ? &lg : nullptr; }
   std::vector<bchdav_iter_record> history;
   // filter SpMM schedules found by timing (block size of the row kernel per matrix and width)
@@ -133,7 +134,7 @@ struct bchdav_handle_s {
                      &small, &norm0, &val32, &R, &hrow, &hcol, &hval, &hvinit, &hev, &hevec, &Rres,
                      &mix, &oz, &oz_vt, &oz_vr, &oz_xt, &oz_bw, &oz_part, &tc_err, &lg_cnt,
                      &lg_off, &lg_tiles, &lg_row, &lg_pseg, &gnn, &gnn_opt, &gnn_w, &km, &km_x,
-                     &lz, &vchk};
+                     &lz, &vchk, &vallo, &ddx};
     for (DevBuf* b : all) f(b);
   }
   size_t held_bytes() {

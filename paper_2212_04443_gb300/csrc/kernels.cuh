@@ -46,6 +46,21 @@ cudaError_t launch_spmm_resid(cudaStream_t st, int n, const int* rowptr, const i
                               const double* d, double* partial, int* n_parts, double* Rout,
                               int ldr, double* negd, const SpmmLong* lg = nullptr);
 int spmm_resid_max_parts(int n, int b);
+// Double-float products for the mixed path (A's values as float hi + lo: vh = the float32
+// copy, vl = launch_split_dd_vec of the float64 values): Y = alpha A X + diag(delta) R and the
+// Step-12 residual, with float64 blocks in and out.  b a multiple of 4 (<= 128), no long rows;
+// scratch holds spmm_dd_scratch_floats(n, b) floats.
+bool spmm_dd_supported(int b, const SpmmLong* lg);
+size_t spmm_dd_scratch_floats(int n, int b);
+cudaError_t launch_split_dd_vec(cudaStream_t st, long long n, const double* v, float* lo);
+cudaError_t launch_spmm_dd(cudaStream_t st, int n, const int* rowptr, const int* colidx,
+                           const float* vh, const float* vl, const double* X, int ldx, int b,
+                           double* Y, int ldy, double alpha, const double* R, int ldr,
+                           const double* delta, float* scratch);
+cudaError_t launch_spmm_resid_dd(cudaStream_t st, int n, const int* rowptr, const int* colidx,
+                                 const float* vh, const float* vl, const double* V, int ldv,
+                                 int b, const double* d, double* partial, int* n_parts,
+                                 double* Rout, int ldr, double* negd, float* scratch);
 
 // ---------------- dense family (dense.cu) ----------------
 // partial[c] = A(rows of chunk c, 0:ka)^T B(rows of chunk c, 0:kb); ka*kb outputs.

@@ -867,6 +867,18 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     val32 = h->val32.as<float>();
   }
   BCHDAV_TRY(prepare_long_rows(h, A, (size_t)std::max(2 * b, 64) * sizeof(double)));
+  // mixed path: Steps 7 and 12 as double-float products (A's values as float hi + lo, hi the
+  // float32 copy of the filter), where the block width allows and no row is segmented
+  const bool dd = prec == BCHDAV_PREC_MIXED && spmm_dd_supported(b, h->long_rows());
+  const float* val_lo = nullptr;
+  float* dd_scr = nullptr;
+  if (dd) {
+    BCHDAV_TRY(h->ensure(h->vallo, (size_t)A->nnz * sizeof(float)));
+    BCHDAV_TRY(h->ensure(h->ddx, spmm_dd_scratch_floats(N, b) * sizeof(float)));
+    HCUDA(launch_split_dd_vec(st, A->nnz, A->val, h->vallo.as<float>()));
+    val_lo = h->vallo.as<float>();
+    dd_scr = h->ddx.as<float>();
+  }
   double* V = h->V.as<double>();
   double* W = h->W.as<double>();
   double* Vtmp = h->Vtmp.as<double>();
@@ -967,8 +979,13 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     tm_orth.stop(st);
     // Step 7: W(:, k_act+1 : k_act+b) = A V_new
     tm_spmm.start(st);
-    HCUDA(launch_spmm_axpby<double>(st, N, A->rowptr, A->colidx, A->val, Xo, ldb, b, W, ldb,
-                                    nullptr, 0, 1.0, 0.0, 0.0, nullptr, 0, nullptr, h->long_rows()));
+    if (dd)
+      HCUDA(launch_spmm_dd(st, N, A->rowptr, A->colidx, val32, val_lo, Xo, ldb, b, W, ldb, 1.0,
+                           nullptr, 0, nullptr, dd_scr));
+    else
+      HCUDA(launch_spmm_axpby<double>(st, N, A->rowptr, A->colidx, A->val, Xo, ldb, b, W, ldb,
+                                      nullptr, 0, 1.0, 0.0, 0.0, nullptr, 0, nullptr,
+                                      h->long_rows()));
     tm_spmm.stop(st);
     ++n_spmm;
     k_act += b;
@@ -1035,9 +1052,14 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     const int nres = nt;
     tm_res.start(st);
     int nparts = 0;
-    HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c, ldv, nres, Dd,
-                            h->part.as<double>(), &nparts, h->Rres.as<double>(), ldr,
-                            negd, h->long_rows()));
+    if (dd && nres % 4 == 0)
+      HCUDA(launch_spmm_resid_dd(st, N, A->rowptr, A->colidx, val32, val_lo, V + k_c, ldv, nres,
+                                 Dd, h->part.as<double>(), &nparts, h->Rres.as<double>(), ldr,
+                                 negd, dd_scr));
+    else
+      HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c, ldv, nres, Dd,
+                              h->part.as<double>(), &nparts, h->Rres.as<double>(), ldr, negd,
+                              h->long_rows()));
     HCUDA(launch_reduce_partials(st, h->part.as<double>(), nparts, 2 * nres, dsel, 1.0));
     HCUDA(cudaMemcpyAsync(hp + act_max + 1, dsel, 2 * nres * sizeof(double), cudaMemcpyDeviceToHost,
                           st));
@@ -1084,9 +1106,14 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
       if (n_ext > 0) {
         int np2 = 0;
         tm_res2.start(st);
-        HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c + nt, ldv, n_ext,
-                                Dd + nt, h->part.as<double>(), &np2, h->Rres.as<double>() + nt,
-                                ldr, negd, h->long_rows()));
+        if (dd && n_ext % 4 == 0)
+          HCUDA(launch_spmm_resid_dd(st, N, A->rowptr, A->colidx, val32, val_lo, V + k_c + nt, ldv,
+                                     n_ext, Dd + nt, h->part.as<double>(), &np2,
+                                     h->Rres.as<double>() + nt, ldr, negd, dd_scr));
+        else
+          HCUDA(launch_spmm_resid(st, N, A->rowptr, A->colidx, A->val, V + k_c + nt, ldv, n_ext,
+                                  Dd + nt, h->part.as<double>(), &np2, h->Rres.as<double>() + nt,
+                                  ldr, negd, h->long_rows()));
         tm_res2.stop(st);
         ++n_spmm;
         n_avail = nt + n_ext;

@@ -320,6 +320,147 @@ template cudaError_t launch_spmm_axpby<float>(cudaStream_t, int, const int*, con
                                               const float*, int, float, float, float, const float*,
                                               int, const float*, const SpmmLong*, int);
 
+// ---------------- double-float products (mixed path, Steps 7 and 12) ----------------
+// y = A x with A's values and x as unevaluated sums of two floats (hi + lo, ~48 significant
+// bits), accumulated in the same form: an exact product error by FMA (two-product) and an
+// error-free two-sum per term, about ten float32 operations where float64 takes one FMA.
+// GB300's float32 pipe is 64 times wider than its float64 pipe, so the product becomes bound by
+// its gathers (the same bytes as float64) instead of float64 arithmetic.  Relative error per
+// output about 2^-46 of sum |a_ij x_j|.  The block x is first split into hi/lo floats,
+// interleaved per four columns ([4 hi][4 lo], 32 bytes per column group), so that one thread's
+// gather is one 32-byte sector.
+__global__ void split_dd_kernel(int n, int b, const double* __restrict__ X, int ldx,
+                                float* __restrict__ XD) {
+  const int g4 = b >> 2;
+  const long long total = (long long)n * g4;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(i / g4), g = (int)(i - (long long)row * g4);
+    const double* x = X + (size_t)row * ldx + 4 * g;
+    float h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      h[j] = __double2float_rn(x[j]);
+      l[j] = __double2float_rn(x[j] - (double)h[j]);
+    }
+    float4* o = reinterpret_cast<float4*>(XD + ((size_t)row * g4 + g) * 8);
+    o[0] = make_float4(h[0], h[1], h[2], h[3]);
+    o[1] = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+__global__ void split_dd_vec_kernel(long long n, const double* __restrict__ v,
+                                    float* __restrict__ lo) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double x = v[i];
+    lo[i] = __double2float_rn(x - (double)__double2float_rn(x));
+  }
+}
+
+// (sh, sl) += (ah + al)(xh + xl).  The rounded product and sums are explicit intrinsics so that
+// none is contracted into an FMA: p must be the same rounded value in the error term and the
+// two-sum.
+__device__ __forceinline__ void dd_fma(float& sh, float& sl, float ah, float al, float xh, float xl) {
+  const float p = __fmul_rn(ah, xh);
+  float e = fmaf(ah, xh, -p);   // exact: ah xh - p
+  e = fmaf(ah, xl, e);
+  e = fmaf(al, xh, e);
+  const float s = __fadd_rn(sh, p);
+  const float z = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = s;
+}
+
+// Y = alpha (A X) + diag(delta) R (R optional), float64 in and out; b a multiple of 4, no long
+// rows.  tpr = b / 4 threads per row, each four columns.
+__global__ void __launch_bounds__(256) spmm_dd_kernel(
+    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+    const float* __restrict__ vh, const float* __restrict__ vl, const float* __restrict__ XD,
+    int b, double* __restrict__ Y, int ldy, double alpha, const double* __restrict__ R, int ldr,
+    const double* __restrict__ delta, int tpr, int rpb) {
+  const int t = threadIdx.x;
+  const int rl = t / tpr;
+  if (rl >= rpb) return;
+  const int row = blockIdx.x * rpb + rl;
+  if (row >= n) return;
+  const int g = t - rl * tpr, c0 = 4 * g, g4 = b >> 2;
+  float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+  const int p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
+  for (int k = p0; k < p1; k += 4) {
+    int j[4];
+    float ah[4], al[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool ok = k + u < p1;
+      j[u] = ok ? __ldg(colidx + k + u) : row;
+      ah[u] = ok ? __ldg(vh + k + u) : 0.f;
+      al[u] = ok ? __ldg(vl + k + u) : 0.f;
+    }
+    float4 xh[4], xl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4* q = reinterpret_cast<const float4*>(XD + ((size_t)j[u] * g4 + g) * 8);
+      xh[u] = __ldg(q);
+      xl[u] = __ldg(q + 1);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (k + u < p1) {
+        dd_fma(sh[0], sl[0], ah[u], al[u], xh[u].x, xl[u].x);
+        dd_fma(sh[1], sl[1], ah[u], al[u], xh[u].y, xl[u].y);
+        dd_fma(sh[2], sl[2], ah[u], al[u], xh[u].z, xl[u].z);
+        dd_fma(sh[3], sl[3], ah[u], al[u], xh[u].w, xl[u].w);
+      }
+    }
+  }
+  double out[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = alpha * ((double)sh[i] + (double)sl[i]);
+  if (R != nullptr) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = fma(__ldg(delta + c0 + i), R[(size_t)row * ldr + c0 + i], out[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Y[(size_t)row * ldy + c0 + i] = out[i];
+}
+
+bool spmm_dd_supported(int b, const SpmmLong* lg) {
+  return b >= 4 && b % 4 == 0 && b <= 128 && (lg == nullptr || lg->n_seg == 0);
+}
+
+size_t spmm_dd_scratch_floats(int n, int b) { return (size_t)n * 2 * (size_t)b + 64; }
+
+cudaError_t launch_split_dd_vec(cudaStream_t st, long long n, const double* v, float* lo) {
+  if (n <= 0) return cudaSuccess;
+  const long long grid = std::min<long long>((n + 255) / 256, 16LL * kSMs);
+  split_dd_vec_kernel<<<(unsigned)grid, 256, 0, st>>>(n, v, lo); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmm_dd(cudaStream_t st, int n, const int* rowptr, const int* colidx,
+                           const float* vh, const float* vl, const double* X, int ldx, int b,
+                           double* Y, int ldy, double alpha, const double* R, int ldr,
+                           const double* delta, float* scratch) {
+  if (n <= 0 || b <= 0) return cudaSuccess;
+  if (b % 4 != 0 || b > 128) return cudaErrorInvalidValue;
+  const long long items = (long long)n * (b / 4);
+  const long long sg = std::min<long long>((items + 255) / 256, 16LL * kSMs);
+  split_dd_kernel<<<(unsigned)sg, 256, 0, st>>>(n, b, X, ldx, scratch); note_launch();
+  const int tpr = b / 4;
+  const int rpb = std::max(1, 256 / tpr);
+  spmm_dd_kernel<<<ceil_div(n, rpb), rpb * tpr, 0, st>>>(n, rowptr, colidx, vh, vl, scratch, b, Y,
+                                                         ldy, alpha, R, ldr, delta, tpr, rpb);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmm_resid_dd(cudaStream_t st, int n, const int* rowptr, const int* colidx,
+                                 const float* vh, const float* vl, const double* V, int ldv,
+                                 int b, const double* d, double* partial, int* n_parts,
+                                 double* Rout, int ldr, double* negd, float* scratch);
+
 // ---------------- residual norms (Step 12) ----------------
 // R = A V - V diag(d) through the row kernel (all rows in flight at once; the product's
 // epilogue subtracts d_j v_j), then one streaming pass for the per-CTA partial sums of r_j^2
@@ -374,6 +515,24 @@ cudaError_t launch_spmm_resid(cudaStream_t st, int n, const int* rowptr, const i
   negate_kernel<<<1, 64, 0, st>>>(b, d, negd); note_launch();
   cudaError_t e = launch_spmm_axpby<double>(st, n, rowptr, colidx, val, V, ldv, b, Rout, ldr,
                                             nullptr, 0, 1.0, 0.0, 0.0, V, ldv, negd, lg);
+  if (e != cudaSuccess) return e;
+  const int grid = spmm_resid_max_parts(n, b);
+  *n_parts = grid;
+  resid_norms_kernel<<<grid, kResidThreads, 0, st>>>(n, Rout, ldr, V, ldv, b, partial);
+  note_launch();
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_spmm_resid_dd(cudaStream_t st, int n, const int* rowptr, const int* colidx,
+                                 const float* vh, const float* vl, const double* V, int ldv,
+                                 int b, const double* d, double* partial, int* n_parts,
+                                 double* Rout, int ldr, double* negd, float* scratch) {
+  if (b > kResidThreads || b <= 0 || Rout == nullptr || negd == nullptr || ldr < b)
+    return cudaErrorInvalidValue;
+  negate_kernel<<<1, 64, 0, st>>>(b, d, negd); note_launch();
+  cudaError_t e = launch_spmm_dd(st, n, rowptr, colidx, vh, vl, V, ldv, b, Rout, ldr, 1.0, V, ldv,
+                                 negd, scratch);
   if (e != cudaSuccess) return e;
   const int grid = spmm_resid_max_parts(n, b);
   *n_parts = grid;

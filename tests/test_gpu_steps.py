@@ -227,6 +227,25 @@ def test_eigh_known_spectrum_with_repeats(H):
     assert np.abs(S @ Y - Y * D).max() < 1e-12
 
 
+@pytest.mark.parametrize("spacing", [0.0, 1e-13, 1e-9])
+def test_eigh_tight_clusters(H, spacing):
+    """Clusters of eigenvalues that the tridiagonal route treats together: exact repeats, a chain
+    1e-13 apart (wider than the route accepts, 1e3 eps ||T||, so the Jacobi kernel behind it
+    takes over on the device) and a chain 1e-9 apart (separate eigenvalues whose vectors are
+    computed independently and orthogonalised by the Newton-Schulz step)."""
+    import torch
+    n = 150
+    Q = np.linalg.qr(synth.gaussian_block(n, n, 21))[0]
+    d = np.concatenate([0.3 + spacing * np.arange(25), np.linspace(0.5, 1.8, n - 25)])
+    S = (Q * d) @ Q.T
+    S = (S + S.T) / 2
+    D, Y = H.eigh(torch.from_numpy(S).cuda())
+    D, Y = to_np(D), to_np(Y)
+    assert np.abs(D - np.sort(d)).max() < 1e-13
+    assert np.abs(Y.T @ Y - np.eye(n)).max() < 1e-12
+    assert np.abs(S @ Y - Y * D).max() < 1e-12
+
+
 def test_eigh_diagonal_plus_border(H):
     """The shape Step 15 leaves for Step 9: diag(d) bordered by k_b new columns."""
     import torch
