@@ -329,6 +329,31 @@ template cudaError_t launch_spmm_axpby<float>(cudaStream_t, int, const int*, con
 // output about 2^-46 of sum |a_ij x_j|.  The block x is first split into hi/lo floats,
 // interleaved per four columns ([4 hi][4 lo], 32 bytes per column group), so that one thread's
 // gather is one 32-byte sector.
+// x = h + l (l exact up to its float rounding, |l| <= ulp(h) / 2), from the bit pattern with
+// integer operations and one int -> float conversion: float64 conversions would run on the
+// narrow float64 pipe.  |x| outside [2^-60, 2^61) takes the float64 conversions.
+__device__ __forceinline__ void dd_split(double x, float& h, float& l) {
+  const long long bits = __double_as_longlong(x);
+  const int ef = (int)((bits >> 52) & 0x7FF);
+  if (ef < 1023 - 60 || ef > 1023 + 60) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+    return;
+  }
+  const unsigned neg = (unsigned)((unsigned long long)bits >> 63) << 31;
+  const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);   // |x| = m 2^(ef - 1075)
+  long long mh = (m + (1LL << 28)) >> 29;                           // leading 24 bits, rounded
+  const int r = (int)(m - (mh << 29));                              // |r| <= 2^28
+  int eh = ef - 1023;
+  if (mh == (1LL << 24)) {
+    mh >>= 1;
+    ++eh;
+  }
+  h = __uint_as_float(neg | ((unsigned)(eh + 127) << 23) | ((unsigned)mh & 0x7FFFFFu));
+  const float fr = __int2float_rn(r);   // r 2^(ef - 1075): shift the exponent field
+  l = (r == 0) ? 0.f : __uint_as_float((__float_as_uint(fr) + ((unsigned)(ef - 1075) << 23)) ^ neg);
+}
+
 __global__ void split_dd_kernel(int n, int b, const double* __restrict__ X, int ldx,
                                 float* __restrict__ XD) {
   const int g4 = b >> 2;
@@ -339,10 +364,7 @@ __global__ void split_dd_kernel(int n, int b, const double* __restrict__ X, int 
     const double* x = X + (size_t)row * ldx + 4 * g;
     float h[4], l[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      h[j] = __double2float_rn(x[j]);
-      l[j] = __double2float_rn(x[j] - (double)h[j]);
-    }
+    for (int j = 0; j < 4; ++j) dd_split(x[j], h[j], l[j]);
     float4* o = reinterpret_cast<float4*>(XD + ((size_t)row * g4 + g) * 8);
     o[0] = make_float4(h[0], h[1], h[2], h[3]);
     o[1] = make_float4(l[0], l[1], l[2], l[3]);
@@ -353,8 +375,9 @@ __global__ void split_dd_vec_kernel(long long n, const double* __restrict__ v,
                                     float* __restrict__ lo) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double x = v[i];
-    lo[i] = __double2float_rn(x - (double)__double2float_rn(x));
+    float h, l;
+    dd_split(v[i], h, l);
+    lo[i] = l;
   }
 }
 
