@@ -666,7 +666,8 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
 }
 
 cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
-                             int ldy, double* work, int* status, int grid_cap) {
+                             int ldy, double* work, int* status, int grid_cap, cudaStream_t aux,
+                             cudaEvent_t ev1, cudaEvent_t ev2) {
   if (n <= 32) return launch_eigh(st, n, H, ldh, D, Y, ldy, work, status);
   if (n > 1024) return cudaErrorInvalidValue;
   const int np = n + (n & 1);
@@ -711,7 +712,7 @@ cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, d
   int* run_if = nullptr;
   if (n <= kTrdMaxN) {
     cudaError_t et = launch_trd_eigh(st, n, H, ldh, D, Y, ldy, work + jacobi_work_doubles(n),
-                                     &run_if);
+                                     &run_if, aux, ev1, ev2);
     if (et == cudaErrorNotSupported) {
       run_if = nullptr;
     } else if (et != cudaSuccess) {

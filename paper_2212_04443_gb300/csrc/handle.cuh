@@ -23,6 +23,32 @@ struct DevBuf {
 struct bchdav_handle_s {
   cudaStream_t stream = nullptr;
   bool owns_stream = false;   // created by the library (batched workers): destroyed with it
+  // second stream and two events for work that runs beside the main stream (Step 9 accumulates
+  // Q there); created on first use, ordered against `stream` by the events only
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
+  bool ensure_aux_stream() {
+    if (aux_stream) return true;
+    if (cudaStreamCreateWithFlags(&aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&aux_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&aux_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      release_aux_stream();
+      return false;
+    }
+    return true;
+  }
+  void release_aux_stream() {
+    if (aux_stream) {
+      cudaStreamSynchronize(aux_stream);
+      cudaStreamDestroy(aux_stream);
+    }
+    for (cudaEvent_t& e : aux_ev) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
+    aux_stream = nullptr;
+  }
   int device = 0;
   // > 0: block cap of the cooperative kernels (1 for handles whose kernels may run beside
   // another handle's, so that no cooperative grid can be left partly resident)
@@ -144,6 +170,7 @@ struct bchdav_handle_s {
   }
 
   void release_all() {
+    release_aux_stream();
     lg = bchdav::SpmmLong();
     for_each_buf([](DevBuf* b) { b->release(); });
     for (bchdav_handle_s* w : workers) {

@@ -184,8 +184,12 @@ cudaError_t launch_eigh(cudaStream_t st, int n, const double* H, int ldh, double
 size_t eigh_work_doubles(int n);
 // Same result by parallel cyclic Jacobi over many SMs for n > 32 (launch_eigh below that);
 // work holds eigh_fast_work_doubles(n) doubles.
+// aux, ev1, ev2 (optional, all or none): a second stream and two events on which the
+// tridiagonal route accumulates Q beside the eigenvalue and eigenvector kernels.
 cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
-                             int ldy, double* work, int* status, int grid_cap = 0);
+                             int ldy, double* work, int* status, int grid_cap = 0,
+                             cudaStream_t aux = nullptr, cudaEvent_t ev1 = nullptr,
+                             cudaEvent_t ev2 = nullptr);
 size_t eigh_fast_work_doubles(int n);
 // Tridiagonal route of launch_eigh_fast for 32 < n <= kTrdMaxN (one thread-block cluster
 // reduces H; eigenvalues and vectors of T on the whole GPU).  work holds trd_work_doubles(n)
@@ -194,7 +198,9 @@ size_t eigh_fast_work_doubles(int n);
 constexpr int kTrdMaxN = 448;
 size_t trd_work_doubles(int n);
 cudaError_t launch_trd_eigh(cudaStream_t st, int n, const double* H, int ldh, double* D,
-                            double* Y, int ldy, double* work, int** run_jacobi);
+                            double* Y, int ldy, double* work, int** run_jacobi,
+                            cudaStream_t aux = nullptr, cudaEvent_t ev_reduced = nullptr,
+                            cudaEvent_t ev_q = nullptr);
 
 // ---------------- Laplacian assembly (laplacian.cu) ----------------
 struct LapWork;

@@ -745,8 +745,10 @@ bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t l
   const size_t wd = std::max(eigh_work_doubles(n), eigh_fast_work_doubles(n));
   BCHDAV_TRY(h->ensure(h->eigw, wd * sizeof(double) + 64));
   int* status_d = reinterpret_cast<int*>(h->eigw.as<char>() + wd * sizeof(double));
+  const bool aux = h->ensure_aux_stream();
   HCUDA(launch_eigh_fast(h->stream, n, H, ld_h, D, Y, ld_y, h->eigw.as<double>(), status_d,
-                         h->coop_grid_cap));
+                         h->coop_grid_cap, aux ? h->aux_stream : nullptr,
+                         aux ? h->aux_ev[0] : nullptr, aux ? h->aux_ev[1] : nullptr));
   int st = 0;
   HCUDA(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HCUDA(cudaStreamSynchronize(h->stream));
@@ -1017,8 +1019,12 @@ bchdav_status bchdav_solve(bchdav_handle h, const bchdav_csr* A, int32_t k, int3
     tm_h.stop(st);
     // Step 9: H Y = Y D (ascending)
     tm_eig.start(st);
-    HCUDA(launch_eigh_fast(st, k_act, Hm, act_max, Dd, Ym, act_max, h->eigw.as<double>(),
-                           eig_status, h->coop_grid_cap));
+    {
+      const bool aux = h->ensure_aux_stream();
+      HCUDA(launch_eigh_fast(st, k_act, Hm, act_max, Dd, Ym, act_max, h->eigw.as<double>(),
+                             eig_status, h->coop_grid_cap, aux ? h->aux_stream : nullptr,
+                             aux ? h->aux_ev[0] : nullptr, aux ? h->aux_ev[1] : nullptr));
+    }
     tm_eig.stop(st);
     HCUDA(cudaMemcpyAsync(hp, Dd, k_act * sizeof(double), cudaMemcpyDeviceToHost, st));
     HCUDA(cudaMemcpyAsync(hp + act_max, eig_status, sizeof(int), cudaMemcpyDeviceToHost, st));

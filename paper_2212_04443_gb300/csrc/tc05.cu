@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_kernel(
   } else {
     // fold warps: tensor-memory lanes 32 (warp % 4) .. + 31
     const int q = warp & 3;
+    const bool small_k = MODE != 2 && nk <= 2;
     long long f = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < wk.n_units && ok; u += gridDim.x) {
@@ -372,7 +373,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_slice_kernel(
             }
             const int col = nt * kTcN + g * 8 + i;
             if (col < wk.ncols && row_ok) {
-              const double v = fma((double)hi, (double)(1LL << (6 * (NS - kH))), (double)lo);
+              // K <= 32 (one or two k steps): every level sum is below 2^20, so the whole
+              // integer fits in 64 bits and one conversion suffices
+              const double v =
+                  small_k ? (double)(hi * (1LL << (6 * (NS - kH))) + lo)
+                          : fma((double)hi, (double)(1LL << (6 * (NS - kH))), (double)lo);
               const int Eb = MODE == 2 ? EB[(size_t)ch * strideB + col] : EB[col];
               acc[g * 8 + i] = fma(v, tc_pow2(Ea + Eb - 6 * (NS + 1)), acc[g * 8 + i]);
             }

@@ -58,7 +58,7 @@ struct TrdCtl {
 };
 
 struct TrdLayout {
-  double *Q, *Zt, *P, *G, *d, *e, *dn, *e2n, *lam, *scr;
+  double *Q, *Zt, *P, *G, *Vr, *tau, *d, *e, *dn, *e2n, *lam, *scr;
   int *bstart, *bend, *rank;
   TrdCtl* ctl;
 };
@@ -70,7 +70,9 @@ __host__ __device__ inline TrdLayout trd_layout(double* w, int n) {
   L.Zt = L.Q + nn;
   L.P = L.Zt + nn;
   L.G = L.P + nn;
-  L.scr = L.G + nn;             // 6 n per eigenvalue: LU factors of T - lambda I
+  L.Vr = L.G + nn;              // reflector i in row i (entries i+1 .. n-1)
+  L.tau = L.Vr + nn;
+  L.scr = L.tau + n;            // 6 n per eigenvalue: LU factors of T - lambda I
   L.d = L.scr + 6 * nn;
   L.e = L.d + n;
   L.dn = L.e + n;               // d / ||T||
@@ -105,11 +107,9 @@ __device__ __forceinline__ double trd_block_sum(double v, double* s_red) {
 // shared-memory layout of trd_reduce_kernel (doubles)
 struct TrdSmem {
   double* A;      // own rows of the working matrix, kTrdMaxRows x ldA
-  double* Qc;     // own columns of Q, kTrdMaxRows x n (column-major: Qc[lc * n + r])
   double* xb;     // [2][n] the column being reduced (pushed by its owners), by parity
   double* pf;     // [n] p = tau A v, pushed by its owners
   double* w;      // [n] w = p - K v
-  double* vq;     // [2][n] reflector v during the accumulation of Q, by parity
   double* taus;   // [n]
   double* sq;     // [kTrdCl] partial sums of squares of the pushed column
   double* pv;     // [kTrdCl] partial p^T v
@@ -121,20 +121,17 @@ struct TrdSmem {
 
 __host__ __device__ inline size_t trd_smem_doubles(int n) {
   const int ldA = n | 1;
-  return (size_t)kTrdMaxRows * ldA + (size_t)kTrdMaxRows * n + 2 * (size_t)n + 2 * (size_t)n +
-         2 * (size_t)n + (size_t)n + 2 * (size_t)kTrdCl + 64 + 32 + 32 + 8;
+  return (size_t)kTrdMaxRows * ldA + 5 * (size_t)n + 2 * (size_t)kTrdCl + 64 + 32 + 32 + 8;
 }
 
 __device__ inline TrdSmem trd_smem(double* base, int n) {
   TrdSmem S;
   const int ldA = n | 1;
   S.A = base;
-  S.Qc = S.A + (size_t)kTrdMaxRows * ldA;
-  S.xb = S.Qc + (size_t)kTrdMaxRows * n;
+  S.xb = S.A + (size_t)kTrdMaxRows * ldA;
   S.pf = S.xb + 2 * n;
   S.w = S.pf + n;
-  S.vq = S.w + n;
-  S.taus = S.vq + 2 * n;
+  S.taus = S.w + n;
   S.sq = S.taus + n;
   S.pv = S.sq + kTrdCl;
   S.red = S.pv + kTrdCl;
@@ -205,7 +202,6 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
   for (int idx = t; idx < nown * n; idx += kTrdThreads) {
     const int lr = idx / n, c = idx - lr * n, r = me + kTrdCl * lr;
     S.A[lr * ldA + c] = (r <= c) ? H[(size_t)r * ldh + c] : H[(size_t)c * ldh + r];
-    S.Qc[lr * n + c] = (c == r) ? 1.0 : 0.0;   // column (me + kTrdCl lr) of I, entry c
   }
   // column 0 (rows 1..n-1) goes to every CTA's xb[0] by its owners, with partial squares of
   // rows 2..n-1
@@ -375,35 +371,55 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
       L.ctl->run_jacobi = 0;
     }
   }
-  // ---- Q = P_0 ... P_{n-3}, backwards; own columns c = me + kTrdCl * lc
-  const int ncol = nown;
-  // v_i (rows i+1 .. n-1) gathered from the owners of the rows: thread t fetches entries
-  // q = t, t + 256, ... of the next reflector while the current one is applied
+  // the reflectors for trd_qform_kernel: v_i (rows i+1 .. n-1, v_i(i+1) = 1) into row i of Vr
+  for (int idx = t; idx < nown * n; idx += kTrdThreads) {
+    const int lr = idx / n, i = idx - lr * n, r = me + kTrdCl * lr;
+    if (i < r - 1) L.Vr[(size_t)i * n + r] = S.A[lr * ldA + i];
+    else if (i == r - 1) L.Vr[(size_t)i * n + r] = 1.0;
+  }
+  if (me == 0)
+    for (int i = t; i < n; i += kTrdThreads) L.tau[i] = (i < n - 2) ? S.taus[i] : 0.0;
+  cl.sync();   // no CTA leaves while others may still read its shared memory
+}
+
+// Q = P_0 P_1 ... P_{n-3}, accumulated backwards (Q <- P_i Q touches rows and columns i+1 ..
+// n-1), columns distributed over the CTAs (column c in CTA c mod gridDim.x, held in shared
+// memory): w^T = v^T Q and Q <- Q - tau v w^T need no exchange, only v_i, read from the
+// reflector rows that trd_reduce_kernel wrote (the next one fetched while the current one is
+// applied).  It runs beside the eigenvalue and eigenvector kernels, on another stream.
+constexpr int kQfCtas = 32;
+
+__global__ void __launch_bounds__(kTrdThreads) trd_qform_kernel(int n, TrdLayout L) {
+  extern __shared__ double sm_qf[];
+  const int me = blockIdx.x, G = gridDim.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int ncol = (n - me + G - 1) / G;        // own columns c = me + G lc
+  double* Qc = sm_qf;                           // ncol x n, column-major
+  double* vq = Qc + (size_t)((n + G - 1) / G) * n;   // [2][n]
+  for (int idx = t; idx < ncol * n; idx += kTrdThreads) {
+    const int lc = idx / n, r = idx - lc * n;
+    Qc[lc * n + r] = (r == me + G * lc) ? 1.0 : 0.0;
+  }
   auto fetch_v = [&](int i, double* dst) {
     const int m = n - i - 1;
-    for (int q = t; q < m; q += kTrdThreads) {
-      const int r = i + 1 + q;
-      dst[q] = (q == 0) ? 1.0 : cl.map_shared_rank(S.A, r % kTrdCl)[(r / kTrdCl) * ldA + i];
-    }
+    for (int q = t; q < m; q += kTrdThreads) dst[q] = __ldcg(L.Vr + (size_t)i * n + i + 1 + q);
   };
-  cl.sync();   // every v is in place
-  if (n >= 3) fetch_v(n - 3, S.vq + ((n - 3) & 1) * n);
+  if (n >= 3) fetch_v(n - 3, vq + ((n - 3) & 1) * n);
   for (int i = n - 3; i >= 0; --i) {
     __syncthreads();   // v_i complete; the other buffer is free
-    if (i >= 1) fetch_v(i - 1, S.vq + ((i - 1) & 1) * n);
-    const double tau = S.taus[i];
+    if (i >= 1) fetch_v(i - 1, vq + ((i - 1) & 1) * n);
+    const double tau = __ldcg(L.tau + i);
     if (tau == 0.0) continue;
-    const double* v = S.vq + (i & 1) * n;
+    const double* v = vq + (i & 1) * n;
     const int m = n - i - 1;
-    const int lc0 = (i + 1 - me + kTrdCl - 1) / kTrdCl;   // first own column > i
-    // a warp's own columns (at most four) at once
+    const int lc0 = (i + 1 - me + G - 1) / G;   // first own column > i
     const int first = lc0 + warp;
     const int cnt = first < ncol ? min(4, (ncol - first + 7) / 8) : 0;
     const double* qr[4];
     double* qc[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      qc[u] = S.Qc + (u < cnt ? first + 8 * u : 0) * n + i + 1;   // rows i+1 .. n-1
+      qc[u] = Qc + (u < cnt ? first + 8 * u : 0) * n + i + 1;   // rows i+1 .. n-1
       qr[u] = qc[u];
     }
     double f[4];
@@ -417,9 +433,8 @@ __global__ void __launch_bounds__(kTrdThreads, 1)
   __syncthreads();
   for (int idx = t; idx < ncol * n; idx += kTrdThreads) {
     const int lc = idx / n, r = idx - lc * n;
-    L.Q[(size_t)r * n + me + kTrdCl * lc] = S.Qc[lc * n + r];
+    L.Q[(size_t)r * n + me + G * lc] = Qc[lc * n + r];
   }
-  cl.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 // Number of eigenvalues of the block [s0, s1) of T / ||T|| below x0 and below x1: the sign
@@ -748,7 +763,7 @@ __global__ void __launch_bounds__(256) trd_gemm_kernel(int n, TrdLayout L, doubl
 
 size_t trd_work_doubles(int n) {
   const size_t nn = (size_t)n * n;
-  return 10 * nn + 5 * (size_t)n + (3 * (size_t)n + 1) / 2 + 2 + sizeof(TrdCtl) / sizeof(double) + 4;
+  return 11 * nn + 6 * (size_t)n + (3 * (size_t)n + 1) / 2 + 2 + sizeof(TrdCtl) / sizeof(double) + 4;
 }
 
 // 0 when this device cannot co-schedule the cluster (the caller keeps the Jacobi route)
@@ -784,7 +799,8 @@ static int trd_cluster_ok(int n) {
 }
 
 cudaError_t launch_trd_eigh(cudaStream_t st, int n, const double* H, int ldh, double* D,
-                            double* Y, int ldy, double* work, int** run_jacobi) {
+                            double* Y, int ldy, double* work, int** run_jacobi, cudaStream_t aux,
+                            cudaEvent_t ev_reduced, cudaEvent_t ev_q) {
   *run_jacobi = nullptr;
   if (!trd_cluster_ok(n)) return cudaErrorNotSupported;
   TrdLayout L = trd_layout(work, n);
@@ -803,8 +819,29 @@ cudaError_t launch_trd_eigh(cudaStream_t st, int n, const double* H, int ldh, do
   note_launch();
   cudaError_t e = cudaLaunchKernelEx(&cfg, trd_reduce_kernel, n, H, ldh, L);
   if (e != cudaSuccess) return e;
+  // Q's accumulation beside the eigenvalues and vectors of T (another stream when given)
+  const size_t qf_smem = ((size_t)ceil_div(n, kQfCtas) * n + 2 * (size_t)n) * sizeof(double);
+  static const bool qf_attr = [] {
+    return cudaFuncSetAttribute(trd_qform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(((size_t)ceil_div(kTrdMaxN, kQfCtas) * kTrdMaxN +
+                                       2 * (size_t)kTrdMaxN) * sizeof(double))) == cudaSuccess;
+  }();
+  if (!qf_attr) return cudaErrorInvalidValue;
+  const bool fork = aux != nullptr && ev_reduced != nullptr && ev_q != nullptr;
+  cudaStream_t sq = fork ? aux : st;
+  if (fork) {
+    e = cudaEventRecord(ev_reduced, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev_reduced, 0);
+    if (e != cudaSuccess) return e;
+  }
+  trd_qform_kernel<<<kQfCtas, kTrdThreads, qf_smem, sq>>>(n, L); note_launch();
   trd_bisect_kernel<<<n, 32, 0, st>>>(n, L); note_launch();
   trd_vectors_kernel<<<ceil_div(n, kTrdEigWarps), kTrdEigWarps * 32, 0, st>>>(n, L); note_launch();
+  if (fork) {
+    e = cudaEventRecord(ev_q, aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_q, 0);
+    if (e != cudaSuccess) return e;
+  }
   const int tiles = ceil_div(n, 16);
   trd_gemm_kernel<0><<<dim3(tiles, tiles, 2), 256, 0, st>>>(n, L, D, Y, ldy); note_launch();
   trd_gemm_kernel<1><<<dim3(tiles, tiles, 1), 256, 0, st>>>(n, L, D, Y, ldy); note_launch();
