@@ -291,7 +291,9 @@ static size_t jacobi_work_doubles(int n) {
 
 // the Jacobi area first (its status word is the route's), the tridiagonal route's after it
 size_t eigh_fast_work_doubles(int n) {
-  return jacobi_work_doubles(n) + (n > 32 && n <= kTrdMaxN ? trd_work_doubles(n) : 0);
+  const size_t small = n <= kEsMaxN ? eig_small_work_doubles() : 0;
+  const size_t trd = n > 32 && n <= kTrdMaxN ? trd_work_doubles(n) : 0;
+  return jacobi_work_doubles(n) + std::max(small, trd);
 }
 
 // player at circle position `pos` in round r (n_pad players, player 0 fixed)
@@ -668,7 +670,8 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_coop_kernel(int n, const d
 cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
                              int ldy, double* work, int* status, int grid_cap, cudaStream_t aux,
                              cudaEvent_t ev1, cudaEvent_t ev2) {
-  if (n <= 32) return launch_eigh(st, n, H, ldh, D, Y, ldy, work, status);
+  const bool small = n <= kEsMaxN && eig_small_available();
+  if (n <= 32 && !small) return launch_eigh(st, n, H, ldh, D, Y, ldy, work, status);
   if (n > 1024) return cudaErrorInvalidValue;
   const int np = n + (n & 1);
   const size_t smem = (size_t)(np / 2) * (2 * sizeof(double) + 4 * sizeof(int));
@@ -707,10 +710,16 @@ cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, d
   JacLayout L = jac_layout(work, n);
   cudaError_t e0 = cudaMemsetAsync(L.status, 0, 6 * sizeof(int), st);   // status, bar, where
   if (e0 != cudaSuccess) return e0;
-  // the tridiagonal route where the device runs it; the Jacobi kernel then runs only when the
-  // route flags its result (a tight cluster too wide, orthogonality out of reach, non-finite H)
+  // the small or the tridiagonal route where the device runs it; the Jacobi kernel then runs
+  // only when the route flags its result (for the small route: the refinement not converged or
+  // a cluster left coupled; for the tridiagonal one: a tight cluster too wide, orthogonality out
+  // of reach; for both: a non-finite H)
   int* run_if = nullptr;
-  if (n <= kTrdMaxN) {
+  if (small) {
+    cudaError_t es = launch_eig_small(st, n, H, ldh, D, Y, ldy, work + jacobi_work_doubles(n),
+                                      &run_if);
+    if (es != cudaSuccess) return es;
+  } else if (n <= kTrdMaxN) {
     cudaError_t et = launch_trd_eigh(st, n, H, ldh, D, Y, ldy, work + jacobi_work_doubles(n),
                                      &run_if, aux, ev1, ev2);
     if (et == cudaErrorNotSupported) {

@@ -182,8 +182,10 @@ size_t inblock_gs_scratch_doubles(int b);
 cudaError_t launch_eigh(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
                         int ldy, double* work, int* status);
 size_t eigh_work_doubles(int n);
-// Same result by parallel cyclic Jacobi over many SMs for n > 32 (launch_eigh below that);
-// work holds eigh_fast_work_doubles(n) doubles.
+// Same result by the small route (n <= kEsMaxN), the tridiagonal route (n <= kTrdMaxN) or
+// parallel cyclic Jacobi over many SMs, which also replaces a route's result that the route
+// flags; launch_eigh for n <= 32 where the device cannot run the small route's cluster.  work
+// holds eigh_fast_work_doubles(n) doubles.
 // aux, ev1, ev2 (optional, all or none): a second stream and two events on which the
 // tridiagonal route accumulates Q beside the eigenvalue and eigenvector kernels.
 cudaError_t launch_eigh_fast(cudaStream_t st, int n, const double* H, int ldh, double* D, double* Y,
@@ -201,6 +203,14 @@ cudaError_t launch_trd_eigh(cudaStream_t st, int n, const double* H, int ldh, do
                             double* Y, int ldy, double* work, int** run_jacobi,
                             cudaStream_t aux = nullptr, cudaEvent_t ev_reduced = nullptr,
                             cudaEvent_t ev_q = nullptr);
+// Small route of launch_eigh_fast for n <= kEsMaxN (eigs.cu): a float32 decomposition refined
+// in float64 by one thread-block cluster.  work holds eig_small_work_doubles() doubles;
+// *run_jacobi as for the tridiagonal route.  eig_small_available(): the device runs the cluster.
+constexpr int kEsMaxN = 64;
+size_t eig_small_work_doubles();
+bool eig_small_available();
+cudaError_t launch_eig_small(cudaStream_t st, int n, const double* H, int ldh, double* D,
+                             double* Y, int ldy, double* work, int** run_jacobi);
 
 // ---------------- Laplacian assembly (laplacian.cu) ----------------
 struct LapWork;
