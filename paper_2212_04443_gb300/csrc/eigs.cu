@@ -27,9 +27,11 @@
 //     Rayleigh quotients lam_j, correct to O(max |E|^2) ||H||.
 //
 // The result is kept when the last update was at most 1e-7 and every pair still inside a
-// cluster is uncoupled (|s_ij| <= 1e-12 ||H||_F: a degenerate eigenvalue, whose vectors may
-// be any orthonormal basis of its space); otherwise, or for a non-finite H, a device word asks
-// the Jacobi kernel that follows to replace it.
+// cluster is uncoupled to the level a backward-stable eigensolver leaves (|s_ij| <= 4e-15 n
+// ||H||_F: a degenerate eigenvalue, whose vectors may be any orthonormal basis of its space);
+// otherwise (a cluster of distinct eigenvalues closer than float32 resolves, which the
+// iteration leaves mixed), or for a non-finite H, a device word asks the Jacobi kernel that
+// follows to replace it.
 #include <cooperative_groups.h>
 
 #include <cfloat>
@@ -49,7 +51,7 @@ constexpr int kEsMaxOwn = (kEsMaxN + kEsCl - 1) / kEsCl;
 constexpr int kEsMaxIt = 6;
 constexpr double kEsStop = 1e-8;
 constexpr double kEsAccept = 1e-7;
-constexpr double kEsCouple = 1e-12;
+constexpr double kEsCouple = 4e-15;   // x n: the coupling a backward-stable result may keep
 
 // control words (the first doubles of the route's work area)
 struct EsCtl {
@@ -679,7 +681,7 @@ __global__ void __launch_bounds__(kEsThreads, 1)
     for (int i = t; i < n && rk < n; i += kEsThreads) Y[(size_t)i * ldy + rk] = Xc[i * ld + j];
   }
   if (me == 0 && t == 0) {
-    const bool ok = emax <= kEsAccept && cpl <= kEsCouple * hnorm;
+    const bool ok = emax <= kEsAccept && cpl <= kEsCouple * n * hnorm;
     ctl->run_jacobi = ok ? 0 : 1;
     ctl->iters = it;
   }
