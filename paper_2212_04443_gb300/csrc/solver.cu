@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -66,10 +67,36 @@ struct Timer {
   }
 };
 
-// Filter SpMM schedule: the row kernel's block size (rows per CTA) for this matrix and block
-// width, chosen by timing each candidate on the first call (the first filter step's own
-// buffers; every candidate computes every row the same way) and cached in the handle.  Small
-// graphs want small blocks (enough CTAs to cover the GPU); large ones fewer, larger blocks.
+// Filter SpMM schedule: the row kernel's block size (rows per CTA) for a matrix and block width.
+// Small graphs want small blocks (enough CTAs to cover the GPU); large ones fewer, larger blocks.
+// The choice is made by timing each candidate on the first filter step's own buffers (every
+// candidate computes every row the same way, so the choice never changes a result) and kept at
+// two levels: per matrix in the handle, and in a process-wide table keyed on the matrix's
+// class -- N and the mean row length in half-octaves, the block width, the value size, and
+// whether long rows are split into segments (the degree skew the row kernel sees) -- so that
+// later matrices of the same class (the graphs of a batch, the next solve) take the entry
+// without timing.  Vector width and the long-row split follow from the block width, alignment
+// and row lengths (spmm.cu).
+struct SpmmClass {
+  int logn2, deg2, b, vsize, skew;
+  bool operator==(const SpmmClass& o) const {
+    return logn2 == o.logn2 && deg2 == o.deg2 && b == o.b && vsize == o.vsize && skew == o.skew;
+  }
+};
+std::mutex g_spmm_class_mu;
+std::vector<std::pair<SpmmClass, int>> g_spmm_class_table;
+
+SpmmClass spmm_class(const bchdav_csr* A, int b, int vsize, bool long_rows) {
+  SpmmClass c;
+  const double n = std::max(1, A->n);
+  c.logn2 = (int)std::floor(2.0 * std::log2(n));
+  c.deg2 = (int)std::floor(2.0 * std::log2(std::max(1.0, (double)A->nnz / n)));
+  c.b = b;
+  c.vsize = vsize;
+  c.skew = long_rows ? 1 : 0;
+  return c;
+}
+
 template <typename F>
 bchdav_status spmm_schedule(bchdav_handle h, const bchdav_csr* A, int b, int vsize, F run,
                             int* threads) {
@@ -78,6 +105,16 @@ bchdav_status spmm_schedule(bchdav_handle h, const bchdav_csr* A, int b, int vsi
       *threads = e.threads;
       return BCHDAV_OK;
     }
+  const SpmmClass cls = spmm_class(A, b, vsize, h->lg.n_seg > 0);
+  {
+    std::lock_guard<std::mutex> lk(g_spmm_class_mu);
+    for (const auto& e : g_spmm_class_table)
+      if (e.first == cls) {
+        *threads = e.second;
+        h->spmm_tune.push_back({A->rowptr, A->n, A->nnz, b, vsize, e.second});
+        return BCHDAV_OK;
+      }
+  }
   cudaStream_t st = h->stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   HCUDA(cudaEventCreate(&e0));
@@ -103,6 +140,12 @@ bchdav_status spmm_schedule(bchdav_handle h, const bchdav_csr* A, int b, int vsi
   cudaEventDestroy(e1);
   HCUDA(err);
   h->spmm_tune.push_back({A->rowptr, A->n, A->nnz, b, vsize, best_t});
+  {
+    std::lock_guard<std::mutex> lk(g_spmm_class_mu);
+    bool found = false;
+    for (const auto& e : g_spmm_class_table) found = found || e.first == cls;
+    if (!found) g_spmm_class_table.push_back({cls, best_t});
+  }
   *threads = best_t;
   return BCHDAV_OK;
 }

@@ -133,6 +133,30 @@ def test_filter_f64_matches_oracle(H, m, a, b):
     assert np.abs(Y - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def test_spmm_schedule_table_shared_by_class(H):
+    """The filter SpMM's block size is timed once per matrix class (N and mean row length in
+    half-octaves, block width, value size, long rows): a second graph of the same class takes
+    the table's entry without the 12 timing launches, a graph of another class is timed."""
+    import torch
+    import paper_2212_04443_gb300 as P
+    b, m = 13, 5          # a block width no other test filters with
+
+    def launches(g):
+        A = device_csr(H, g)
+        X = torch.from_numpy(synth.gaussian_block(g.n, b, 1)).cuda()
+        torch.cuda.synchronize()
+        l0 = P.launch_count()
+        H.filter(A, X, m, 0.1, 2.0, 0.0)
+        torch.cuda.synchronize()
+        return P.launch_count() - l0
+
+    first = launches(synth.sbm_edges(6000, 8, d_in=12, d_out=1.5, seed=71))
+    same = launches(synth.sbm_edges(6000, 8, d_in=12, d_out=1.5, seed=72))
+    other = launches(synth.sbm_edges(90000, 8, d_in=12, d_out=1.5, seed=73))
+    assert first - same == 12
+    assert other - same == 12
+
+
 def test_filter_on_exact_cycle_modes(H):
     import torch
     n, m, a = 1000, 15, 0.35
