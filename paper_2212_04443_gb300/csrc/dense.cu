@@ -130,13 +130,26 @@ cudaError_t launch_gemm_tn_partial(cudaStream_t st, int n, const double* A, int 
   return cudaGetLastError();
 }
 
+// Second stage of the two-stage sums, in a fixed order: four running sums over the chunks
+// c = 0, 1, 2, 3 (mod 4), then (s0 + s1) + (s2 + s3).  Four independent chains: a float64 add
+// waits ~64 cycles for the one before it on GB300, so one chain over a few hundred chunks
+// took 10-20 us.
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n_chunks, int count,
                                        double* __restrict__ out, double scale) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  double s = 0.0;
-  for (int c = 0; c < n_chunks; ++c) s += partial[(size_t)c * count + i];
-  out[i] = scale * s;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int c = 0;
+  for (; c + 3 < n_chunks; c += 4) {
+    s0 += partial[(size_t)c * count + i];
+    s1 += partial[(size_t)(c + 1) * count + i];
+    s2 += partial[(size_t)(c + 2) * count + i];
+    s3 += partial[(size_t)(c + 3) * count + i];
+  }
+  if (c < n_chunks) s0 += partial[(size_t)c * count + i];
+  if (c + 1 < n_chunks) s1 += partial[(size_t)(c + 1) * count + i];
+  if (c + 2 < n_chunks) s2 += partial[(size_t)(c + 2) * count + i];
+  out[i] = scale * ((s0 + s1) + (s2 + s3));
 }
 
 cudaError_t launch_reduce_partials(cudaStream_t st, const double* partial, int n_chunks, int count,
@@ -261,25 +274,44 @@ cudaError_t launch_gemm_tri_inplace(cudaStream_t st, int n, double* X, int ldx, 
 }
 
 // ---------------- column sums of squares ----------------
+// Per-CTA partial sums of squares of X's columns (fixed order: four running sums over the
+// CTA's rows, then over its row groups), so that several loads and float64 chains are in flight
+// per thread.
 __global__ void col_sumsq_kernel(int n, const double* __restrict__ X, int ldx, int b,
                                  double* __restrict__ partial) {
   extern __shared__ double sh[];
   const int t = threadIdx.x;
   const int rpb = blockDim.x / b;
   const int rl = t / b, c = t - rl * b;
-  double s = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   if (rl < rpb) {
-    for (int row = blockIdx.x * rpb + rl; row < n; row += gridDim.x * rpb) {
-      double v = X[(size_t)row * ldx + c];
-      s = fma(v, v, s);
+    const int step = gridDim.x * rpb;
+    int row = blockIdx.x * rpb + rl;
+    for (; row + 3 * step < n; row += 4 * step) {
+      const double v0 = X[(size_t)row * ldx + c], v1 = X[(size_t)(row + step) * ldx + c];
+      const double v2 = X[(size_t)(row + 2 * step) * ldx + c];
+      const double v3 = X[(size_t)(row + 3 * step) * ldx + c];
+      s0 = fma(v0, v0, s0);
+      s1 = fma(v1, v1, s1);
+      s2 = fma(v2, v2, s2);
+      s3 = fma(v3, v3, s3);
+    }
+    for (; row < n; row += step) {
+      const double v = X[(size_t)row * ldx + c];
+      s0 = fma(v, v, s0);
     }
   }
-  sh[t] = (rl < rpb) ? s : 0.0;
+  sh[t] = (rl < rpb) ? (s0 + s1) + (s2 + s3) : 0.0;
   __syncthreads();
   if (t < b) {
-    double a = 0.0;
-    for (int q = 0; q < rpb; ++q) a += sh[q * b + t];
-    partial[(size_t)blockIdx.x * b + t] = a;
+    double a0 = 0.0, a1 = 0.0;
+    int q = 0;
+    for (; q + 1 < rpb; q += 2) {
+      a0 += sh[q * b + t];
+      a1 += sh[(q + 1) * b + t];
+    }
+    if (q < rpb) a0 += sh[q * b + t];
+    partial[(size_t)blockIdx.x * b + t] = a0 + a1;
   }
 }
 

@@ -399,7 +399,9 @@ bchdav_status run_orth(bchdav_handle h, int n, const double* V, int ldv, int k, 
   double* hp = h->host_aux;
 
   auto col_norms = [&](double* out_host) -> bchdav_status {
-    int nc = std::min(chunks, ceil_div(n, 256 / b));
+    // >= 16 rows per thread, within the partial-sum buffer
+    const int nc = (int)std::min<size_t>(std::min(4 * kSMs, ceil_div(n, 256 / b * 16)),
+                                         part_doubles / b);
     HCUDA(launch_col_sumsq_partial(st, n, X, ldx, b, h->part.as<double>(), nc));
     HCUDA(launch_reduce_partials(st, h->part.as<double>(), nc, b, h->G.as<double>(), 1.0));
     HCUDA(cudaMemcpyAsync(hp, h->G.as<double>(), b * sizeof(double), cudaMemcpyDeviceToHost, st));
