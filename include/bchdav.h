@@ -285,13 +285,19 @@ bchdav_status bchdav_gram(bchdav_handle h, int32_t n, const double* A, int32_t l
 bchdav_status bchdav_rotate(bchdav_handle h, int32_t n, double* V, int32_t ldv, int32_t k,
                             const double* Y, int32_t ld_y, int32_t nb, int32_t dense_path);
 
-/* Step 9: H Y = Y D for the symmetric n x n float64 matrix H (ld_h; only the
- * upper triangle is read).  D: n eigenvalues ascending; Y: n x n, column j the
- * eigenvector of D[j] (row-major, ld_y).  All on the device: for n <= 32 one
- * thread block runs Householder tridiagonalisation and implicit-shift QL; for
- * 32 < n <= 1024 a cooperative grid runs parallel cyclic Jacobi (both give the
- * same eigenpairs to rounding).  n outside [1, 1024] returns BCHDAV_ERR_ARG.
- * Synchronises the handle's stream (it reads the convergence status). */
+/* Step 9 (Algorithm 2): H Y = Y D for the symmetric n x n float64 matrix H (ld_h; only the
+ * upper triangle is read).  D: n eigenvalues ascending; Y: n x n, column j the eigenvector of
+ * D[j] (row-major, ld_y).  All on the device, float64-accurate by one of three routes:
+ *  - n <= 64: a float32 decomposition (Householder, multisection, inverse iteration) refined
+ *    in float64 by the Ogita-Aishima iteration, in one thread-block cluster;
+ *  - 64 < n <= 448: Householder tridiagonalisation in one cluster, multisection and inverse
+ *    iteration on the tridiagonal matrix, one Newton-Schulz step;
+ *  - n > 448, and whenever a route flags its result on the device (a cluster of eigenvalues it
+ *    cannot resolve, a refinement that did not settle, a non-finite H): parallel cyclic Jacobi
+ *    on a cooperative grid.
+ * The routes give the same eigenpairs to rounding (vectors of a repeated eigenvalue: any
+ * orthonormal basis of its space).  n outside [1, 1024] returns BCHDAV_ERR_ARG.  Synchronises
+ * the handle's stream (it reads the convergence status). */
 bchdav_status bchdav_eigh(bchdav_handle h, int32_t n, const double* H, int32_t ld_h, double* D,
                           double* Y, int32_t ld_y);
 
@@ -391,10 +397,11 @@ bchdav_status bchdav_spectral_cluster(bchdav_handle h, int32_t n, int32_t dim, c
  * array inside the library (about 384 KiB per GPU, held until the process
  * exits).  Same arguments as bchdav_eigh, plus the CUDA stream (cudaStream_t,
  * NULL = legacy default stream) the work is ordered on; the call synchronises
- * that stream before returning.  It always runs the one-block Householder + QL
- * kernel (bchdav_eigh's path for n <= 32; for 32 < n <= 128 bchdav_eigh runs
- * Jacobi instead), so its results equal bchdav_eigh's to rounding, not bit
- * for bit, and it is slower than bchdav_eigh for the larger n.
+ * that stream before returning.  It always runs one thread block's Householder
+ * tridiagonalisation and implicit-shift QL (bchdav_eigh takes the routes listed
+ * above instead), so its results equal bchdav_eigh's to rounding, not bit for
+ * bit, and it is slower than bchdav_eigh (about 0.25 ms at n = 8, 2.7 ms at
+ * n = 32 on GB300, where float64 chains wait ~64 cycles per operation).
  *  - n must be <= 128; larger n returns BCHDAV_ERR_ARG (message via
  *    bchdav_last_error(NULL)).
  *  - The first call on a device looks up the scratch array's device address

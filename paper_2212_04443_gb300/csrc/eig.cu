@@ -1,5 +1,8 @@
 // Step 9 of Algorithm 2: H Y = Y D for the small symmetric Rayleigh-quotient
-// matrix H (n <= act_max), in float64, on the device.
+// matrix H (n <= act_max), in float64, on the device.  launch_eigh_fast picks the
+// route (eigs.cu for n <= 64, trd.cu up to 448, the Jacobi kernel below beyond that
+// and as the device-gated fallback of both); this file also holds the one-block
+// kernel of the allocation-free entry point and of the Lanczos bounds:
 //
 // Householder reduction to tridiagonal form (P_k = I - 2 v v^T, applied as
 // A <- A - 2 (v w^T + w v^T) with w = A v - (v^T A v) v), backward accumulation
@@ -289,7 +292,7 @@ static size_t jacobi_work_doubles(int n) {
   return 2 * np * np + 2 * 4 * kSMs + 3 * np + 16;
 }
 
-// the Jacobi area first (its status word is the route's), the tridiagonal route's after it
+// the Jacobi area first (its status word is the route's), the small or tridiagonal route's after it
 size_t eigh_fast_work_doubles(int n) {
   const size_t small = n <= kEsMaxN ? eig_small_work_doubles() : 0;
   const size_t trd = n > 32 && n <= kTrdMaxN ? trd_work_doubles(n) : 0;
