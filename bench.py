@@ -171,9 +171,10 @@ def slice_pairs(S):
 
 
 # DRAM bytes (read + write) per launch of the filter SpMM (spmm_axpby_kernel<float, 4>, one
-# residual-form step) on the 1M-node SBM, from the ncu capture of the current kernel
-# (profiles/spmm_axpby_f32_sbm1m.md); None when no capture of the current kernel exists
-FILTER_TRAFFIC_BYTES = {"sbm1m": None}
+# residual-form step) on the 1M-node SBM: dram__bytes_read.sum + dram__bytes_write.sum of three
+# interior filter steps in a one-pass ncu capture of the current kernel (470.4 + 68.6 MB); to
+# be set back to None whenever the kernel changes
+FILTER_TRAFFIC_BYTES = {"sbm1m": 539_027_029}
 
 
 def filter_model_bytes(n, nnz, b, m, iters, s):
