@@ -257,6 +257,15 @@ bchdav_status bchdav_filter(bchdav_handle h, const bchdav_csr* A, const double* 
 bchdav_status bchdav_spmm(bchdav_handle h, const bchdav_csr* A, const double* X, int32_t ldx,
                           int32_t b, double* Y, int32_t ldy);
 
+/* The same product as the mixed path computes it in Steps 7 and 12 of Algorithm 2: A's values
+ * and X's entries as unevaluated sums of two floats (hi + lo; hi of the values = A->val_f32,
+ * required), an exact float product and sum per term, float64 in and out.  Relative error per
+ * entry about 2^-46 of sum_j |a_ij x_j|.  X, Y: device, N x b (ldx, ldy), X != Y; b a multiple
+ * of 4 and at most 128, and no row longer than the SpMM segment length (otherwise
+ * BCHDAV_ERR_ARG: the mixed path then uses the float64 product). */
+bchdav_status bchdav_spmm_dd(bchdav_handle h, const bchdav_csr* A, const double* X, int32_t ldx,
+                             int32_t b, double* Y, int32_t ldy);
+
 /* Step 6: orthonormalise the N x b block X (in place, ldx) against the k
  * orthonormal columns of V (ldv) and among themselves: two classical
  * Gram-Schmidt passes against V, then column-by-column Gram-Schmidt with a

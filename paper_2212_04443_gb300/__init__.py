@@ -35,7 +35,7 @@ STATUS = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "invalid CSR"
 EXPORTED_SYMBOLS = [
     "bchdav_create", "bchdav_destroy", "bchdav_set_stream", "bchdav_status_string",
     "bchdav_last_error", "bchdav_build_laplacian", "bchdav_free_csr", "bchdav_copy_csr", "bchdav_check_csr",
-    "bchdav_solve", "bchdav_solve_host", "bchdav_history", "bchdav_filter", "bchdav_spmm",
+    "bchdav_solve", "bchdav_solve_host", "bchdav_history", "bchdav_filter", "bchdav_spmm", "bchdav_spmm_dd",
     "bchdav_orthonormalize", "bchdav_gram", "bchdav_rotate", "bchdav_eigh",
     "bchdav_eigh_noalloc", "bchdav_solve_batched", "bchdav_set_batch_workers",
     "bchdav_launch_count", "bchdav_gnn_n_params", "bchdav_gnn_forward", "bchdav_gnn_loss_grad",
@@ -139,6 +139,7 @@ def lib() -> C.CDLL:
         "bchdav_gnn_start_block": (i32, [p, C.POINTER(CSRStruct), p, i32, p, i32, i32, p, p]),
         "bchdav_filter": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, i32, d, d, d, i32, p, i32]),
         "bchdav_spmm": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, p, i32]),
+        "bchdav_spmm_dd": (i32, [p, C.POINTER(CSRStruct), p, i32, i32, p, i32]),
         "bchdav_orthonormalize": (i32, [p, i32, p, i32, i32, p, i32, i32, u64, d,
                                         C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
         "bchdav_eigh": (i32, [p, i32, p, i32, p, p, i32]),
@@ -543,6 +544,16 @@ class Handle:
         cs = A.struct()
         self._check(self.L.bchdav_spmm(self.h, C.byref(cs), _ptr(X), X.stride(0), X.shape[1],
                                        _ptr(Y), Y.stride(0)))
+        return Y
+
+    def spmm_dd(self, A: DeviceCSR, X, Y=None):
+        """Y = A X by the mixed path's double-float product (Steps 7 and 12)."""
+        import torch
+        if Y is None:
+            Y = torch.empty_like(X)
+        cs = A.struct()
+        self._check(self.L.bchdav_spmm_dd(self.h, C.byref(cs), _ptr(X), X.stride(0), X.shape[1],
+                                          _ptr(Y), Y.stride(0)))
         return Y
 
     def orthonormalize(self, V, X, *, seed: int = 0, tau_dep: float = 1e-10, rep_counter: int = 0):

@@ -660,6 +660,28 @@ bchdav_status bchdav_spmm(bchdav_handle h, const bchdav_csr* A, const double* X,
   return BCHDAV_OK;
 }
 
+bchdav_status bchdav_spmm_dd(bchdav_handle h, const bchdav_csr* A, const double* X, int32_t ldx,
+                             int32_t b, double* Y, int32_t ldy) {
+  if (!h) return BCHDAV_ERR_ARG;
+  BCHDAV_TRY(check_csr_args(h, A));
+  if (b < 1 || ldx < b || ldy < b || !X || !Y || X == Y || !A->val_f32) {
+    h->set_error(BCHDAV_ERR_ARG, "spmm_dd: bad arguments (A->val_f32 required, X != Y)");
+    return BCHDAV_ERR_ARG;
+  }
+  BCHDAV_TRY(prepare_long_rows(h, A, (size_t)b * sizeof(double)));
+  if (!spmm_dd_supported(b, h->long_rows())) {
+    h->set_error(BCHDAV_ERR_ARG,
+                 "spmm_dd: b must be a multiple of 4 (<= 128) and no row may need segments");
+    return BCHDAV_ERR_ARG;
+  }
+  BCHDAV_TRY(h->ensure(h->vallo, (size_t)A->nnz * sizeof(float)));
+  BCHDAV_TRY(h->ensure(h->ddx, spmm_dd_scratch_floats(A->n, b) * sizeof(float)));
+  HCUDA(launch_split_dd_vec(h->stream, A->nnz, A->val, h->vallo.as<float>()));
+  HCUDA(launch_spmm_dd(h->stream, A->n, A->rowptr, A->colidx, A->val_f32, h->vallo.as<float>(), X,
+                       ldx, b, Y, ldy, 1.0, nullptr, 0, nullptr, h->ddx.as<float>()));
+  return BCHDAV_OK;
+}
+
 bchdav_status bchdav_filter(bchdav_handle h, const bchdav_csr* A, const double* X, int32_t ldx,
                             int32_t b, int32_t m, double a, double upb, double a0,
                             int32_t precision, double* Y, int32_t ldy) {

@@ -80,6 +80,38 @@ def test_spmm_matches_scipy(H, b):
     assert np.abs(Y - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("b", [4, 20, 64])
+def test_spmm_dd_matches_float64(H, b):
+    """The mixed path's double-float product (Steps 7 and 12): within 2^-44 of sum |a_ij x_j|
+    per entry (the pair arithmetic keeps ~48 bits), far inside float64's reach of float32's."""
+    import torch
+    g = synth.sbm_edges(20011, 9, d_in=11, d_out=2, seed=3)
+    A = device_csr(H, g)
+    L = oracle_csr(g)
+    X = synth.gaussian_block(g.n, b, 5)
+    X[7] *= 1e-30                      # tiny and huge entries take the float64 split path
+    X[11] *= 1e30
+    Y = to_np(H.spmm_dd(A, torch.from_numpy(X).cuda()))
+    S = L.scipy()
+    ref = S @ X
+    bound = abs(S) @ np.abs(X)
+    assert np.all(np.abs(Y - ref) <= 2.0 ** -44 * bound)
+    big = bound > 1e-200
+    assert (np.abs(Y - ref)[big] / bound[big]).max() < 1e-12   # not a float32 product
+
+
+def test_spmm_dd_rejects_what_the_mixed_path_keeps_in_float64(H):
+    import torch
+    import paper_2212_04443_gb300 as P
+    g = synth.sbm_edges(3000, 4, d_in=8, d_out=1, seed=2)
+    A = device_csr(H, g)
+    with pytest.raises(P.BchdavError):          # width not a multiple of 4
+        H.spmm_dd(A, torch.zeros((g.n, 6), dtype=torch.float64, device="cuda"))
+    Ah = device_csr(H, _hub_graph())            # rows that need segments
+    with pytest.raises(P.BchdavError):
+        H.spmm_dd(Ah, torch.zeros((Ah.n, 8), dtype=torch.float64, device="cuda"))
+
+
 def _hub_graph():
     """Rows far over the 1024-nonzero segment length (star hubs of 5000 and 2500 leaves, whose
     lengths are not multiples of it) next to power-law and short rows."""
